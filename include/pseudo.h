@@ -1,0 +1,182 @@
+/*
+ * pseudo.h -- C ABI of the B300 (sm_103a) pseudospectra library.
+ *
+ * The library evaluates sigma_min(C - zI) at every point z of a grid, for a
+ * dense square complex matrix C given through its complex Schur factor T
+ * (C = Q T Q^H, T upper triangular; Sec. 2.1 and SM2.1 of the paper:
+ * M = T, S = I, so sigma(C - zI) = sigma(T - zI) and no QR per point is needed).
+ * The epsilon-pseudospectrum is {z : sigma_min(C - zI) < eps} (Sec. 1, eq.
+ * (defSquareSVD)); the library also returns that membership per level.
+ *
+ * Two methods are exposed (pseudo_opts.mode):
+ *   PSEUDO_INVLANC  inverse Lanczos on N(z)^{-1}, N(z) = (T - zI)^H (T - zI),
+ *                   per point, through triangular solves with T - zI
+ *                   (Sec. 1; the EigTool core the paper compares against).
+ *   PSEUDO_RECYCLE  singular-subspace recycling (Alg. 3, psTriRecy): a fast
+ *                   Rayleigh--Ritz-SVD on a recycled basis V (Alg. 1) with a
+ *                   backward-stability test (eq. (tolC)); rejected points are
+ *                   refined by LOBPCG-SVD on (T - zI)^{-H} (Alg. SM1.2) and
+ *                   their singular vectors update V (Alg. 2).
+ *
+ * Conventions for every entry point:
+ *   - Complex numbers are pseudo_c64 {re, im} (layout of cuDoubleComplex and
+ *     of torch.complex128).
+ *   - Return value: PSEUDO_OK (0), a positive warning (results written), or a
+ *     negative error (nothing valid written).  pseudo_last_error() gives a
+ *     thread-local message for the last non-zero return.
+ *   - "device" pointers are CUDA device memory of the handle's device;
+ *     "host" pointers are ordinary host memory.  Which one a pointer is
+ *     is never guessed: it is stated per argument or by a flag.
+ *   - All work is enqueued on the CUDA stream passed in (cudaStream_t cast to
+ *     void*; NULL = legacy default stream).  Calls that return results to
+ *     host memory synchronise that stream before returning.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef PSEUDO_B300_H
+#define PSEUDO_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pseudo_ctx *pseudo_handle;
+typedef struct { double re, im; } pseudo_c64;
+
+enum {
+    PSEUDO_OK = 0,
+    PSEUDO_WARN_NOT_CONVERGED = 1, /* all outputs written; some points flagged */
+    PSEUDO_ERR_ARG = -1,           /* invalid argument (null, size, range) */
+    PSEUDO_ERR_UNSUPPORTED = -2,   /* e.g. m != n (rectangular input) */
+    PSEUDO_ERR_CUDA = -3,          /* a CUDA call failed; see pseudo_last_error */
+    PSEUDO_ERR_WORKSPACE = -4,     /* workspace too small or misaligned */
+    PSEUDO_ERR_NONFINITE = -5,     /* NaN/Inf in T or z */
+    PSEUDO_ERR_TIMEOUT = -6        /* an iteration cap was hit in a fatal place */
+};
+
+enum { PSEUDO_INVLANC = 0, PSEUDO_RECYCLE = 1 };
+enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
+
+/* per-point flags (flags_out) */
+enum {
+    PSEUDO_PT_ACCEPTED = 1,      /* recycled Ritz value accepted (no refinement) */
+    PSEUDO_PT_REFINED = 2,       /* refined by LOBPCG-SVD / Lanczos */
+    PSEUDO_PT_NOT_CONVERGED = 4, /* iteration cap hit; best estimate returned */
+    PSEUDO_PT_IR_FALLBACK = 8,   /* mixed precision refinement fell back to FP64 */
+    PSEUDO_PT_SINGULAR = 16      /* z hit a diagonal entry of T to working precision */
+};
+
+/* Options; pseudo_opts_default() fills the paper's parameters (Sec. 4):
+ * r = 6, eta = 1e-4, eps shift = 1e-14 ||C||^2, tau = 1e-10, omega = 1.6,
+ * p_max = 60, b = 20. */
+typedef struct {
+    int mode;           /* PSEUDO_INVLANC | PSEUDO_RECYCLE */
+    int precision;      /* PSEUDO_FP64 | PSEUDO_MIXED (FP32 solves + FP64 refinement) */
+    int r;              /* LOBPCG block size r (paper 6) */
+    int p_max;          /* cap on recycled blocks; k_max = p_max * r */
+    int grid_nx, grid_ny; /* Cartesian layout of z[] (row-major, x fastest); 0 = unordered */
+    int batch_b;        /* column-batch size b of the batch-zigzag traversal (paper 20) */
+    int lanes;          /* independent recycle lanes processed side by side (0 = auto) */
+    int shift_batch;    /* INVLANC: shifts per launch wave (0 = auto) */
+    double eps_shift_rel; /* epsilon = eps_shift_rel * ||T||_2^2 (paper 1e-14) */
+    double tau;         /* eigen-gap tolerance of eq. (tau) (paper 1e-10) */
+    double omega;       /* pruning threshold of eq. (omegaCond) (paper 1.6) */
+    double eta;         /* backward-stability tolerance of eqs. (tolC), (tolSVD) (paper 1e-4) */
+    double rtol;        /* accuracy target on sigma: points are accepted/converged only when
+                           the a-posteriori relative error estimate is <= rtol/4; 0 = paper
+                           tests only */
+    int maxiter_lanczos; /* Lanczos steps cap (<= 120) */
+    int maxiter_lobpcg;  /* LOBPCG iterations cap */
+    int max_ir;          /* iterative-refinement steps cap per solve (mixed precision) */
+    int io_host;        /* 1: z/sigma/res/flags/member pointers of pseudo_grid are host memory */
+    uint64_t seed;      /* seed of the random start vectors */
+} pseudo_opts;
+
+typedef struct {
+    int64_t sv_R;        /* triangular solves with T - zI or its adjoint, one per column */
+    int64_t mv_M;        /* products of T (or T^H) with a vector, one per column */
+    int64_t mv_M_fp64_refine; /* FP64 products spent in iterative refinement */
+    int64_t n_points;
+    int64_t n_accepted;  /* recycle mode: accepted from the recycled subspace */
+    int64_t n_refined;   /* refined points (= recycling points) */
+    int64_t n_not_converged;
+    int64_t n_updates;   /* updateRecy calls */
+    int64_t lanczos_steps;
+    int64_t lobpcg_iters;
+    double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
+} pseudo_stats_t;
+
+/* Fill *o with defaults. Returns PSEUDO_OK or PSEUDO_ERR_ARG (o == NULL). */
+int pseudo_opts_default(pseudo_opts *o);
+
+/* Create a handle from the upper-triangular Schur factor T (SM2.1: M = T, S = I).
+ *   T         : column-major complex n x n with leading dimension ldT >= m;
+ *               only the upper triangle (i <= j) is read.
+ *   t_on_host : 1 if T is host memory, 0 if device memory.
+ *   m, n      : must be equal (rectangular input -> PSEUDO_ERR_UNSUPPORTED).
+ *   stream    : cudaStream_t for the set-up copies/kernels.
+ * The library copies T into handle-owned device buffers (packed FP64 and FP32
+ * panels of T and T^H) -- the only device allocations the library makes; the
+ * caller may free T on return.  Also computes ||T||_F and a 2-norm estimate.
+ * Errors: ARG (null/size), UNSUPPORTED (m != n), NONFINITE, CUDA. */
+int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_on_host,
+                  void *stream, pseudo_handle *out);
+
+/* Bytes of caller-provided device workspace that pseudo_grid needs for npts
+ * points under options o.  Errors: ARG. */
+int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, size_t *bytes);
+
+/* sigma_min(T - z_j I) for j < npts.
+ *   z          : npts complex shifts (device, or host if o->io_host).
+ *   eps_levels : host array of neps (<= 32) levels; may be NULL if neps == 0.
+ *   sigma_out  : npts doubles (device/host as z).
+ *   res_out    : npts doubles or NULL: ||N(z)x - s^2 x|| / (s * (||T||_2,est + |z|)) for the
+ *                returned unit vector x and value s (the quantity eq. (tolC) bounds by eta).
+ *   flags_out  : npts int32 PSEUDO_PT_* bits, or NULL.
+ *   member_out : npts uint32 words, bit i set iff sigma < eps_levels[i] (strict), or NULL.
+ *   workspace  : device memory of >= pseudo_workspace_bytes(...) bytes, 256-byte aligned.
+ * Outputs are in the caller's order of z.  No device memory is allocated.
+ * Returns OK, WARN_NOT_CONVERGED, or an error. */
+int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double *eps_levels,
+                int neps, const pseudo_opts *o, double *sigma_out, double *res_out,
+                int32_t *flags_out, uint32_t *member_out, void *workspace,
+                size_t workspace_bytes, void *stream);
+
+/* Counters and phase timings accumulated since create or the last reset. */
+int pseudo_stats(pseudo_handle h, pseudo_stats_t *out);
+int pseudo_stats_reset(pseudo_handle h);
+
+/* Problem facts of the handle: n, ||T||_F and the 2-norm estimate. */
+int pseudo_info(pseudo_handle h, int64_t *n, double *norm_fro, double *norm2_est);
+
+/* Release the handle and its device buffers.  NULL-safe. */
+void pseudo_destroy(pseudo_handle h);
+
+/* Thread-local message describing the last non-OK return ("" if none). */
+const char *pseudo_last_error(void);
+
+/* ---- kernel-level entry points (used by the tests; same rules as above) ----
+ *
+ * pseudo_solve: X[:, c] <- (T - z_c I)^{-1} X[:, c] (adjoint = 0) or
+ *               (T - z_c I)^{-H} X[:, c] (adjoint = 1) for c < ncols: the
+ *               multi-shift triangular solve that applies R(z)^{-1} and R(z)^{-*}
+ *               (Alg. 3, lobpcgSvd on R(z)^{-*}; sv_R in Table 2).
+ *   X   : device, row-major n x ncols complex (element (i, c) at X[i*ncols + c]).
+ *   z   : device, ncols complex shifts, one per column.
+ *   precision : PSEUDO_FP64 (all FP64) or PSEUDO_MIXED (FP32 arithmetic).
+ *   workspace : device, >= pseudo_solve_workspace_bytes bytes.
+ * pseudo_matvec: Y[:, c] <- B[:, c] - beta * (T - z_c I)^{op} X[:, c] in FP64, with
+ *   beta in {+1, -1} given by subtract (1: B - AX, 0: AX, B ignored and may be NULL).
+ *   X, Y, B device row-major n x ncols complex; Y must not alias X. */
+int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
+int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
+                 int precision, void *workspace, size_t workspace_bytes, void *stream);
+int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
+                  const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

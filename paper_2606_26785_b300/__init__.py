@@ -1,0 +1,164 @@
+"""B300 (sm_103a) pseudospectra library: sigma_min(C - zI) over a grid from
+the complex Schur factor T of C, with hand-written CUDA kernels behind a C ABI
+(include/pseudo.h).  This module is the thin Python binding: it marshals
+arguments (device buffers come from PyTorch) and calls the library; every step
+of the computation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import FP64, INVLANC, MIXED, RECYCLE, Opts, PseudoError, Stats, check  # noqa: F401
+
+__all__ = ["Pseudo", "default_opts", "FP64", "MIXED", "INVLANC", "RECYCLE", "PseudoError"]
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _abi.load().pseudo_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Pseudo:
+    """Handle on one Schur factor T (n x n, upper triangular, complex128)."""
+
+    def __init__(self, T, stream=None):
+        torch = _torch()
+        lib = _abi.load()
+        if isinstance(T, np.ndarray):
+            Tt = torch.from_numpy(np.asfortranarray(T.astype(np.complex128)).T.copy()).cuda()
+        else:
+            Tt = T.to(device="cuda", dtype=torch.complex128).t().contiguous()
+        # Tt holds T^T row-major == T column-major
+        n = Tt.shape[0]
+        h = ctypes.c_void_p()
+        check(lib.pseudo_create(_ptr(Tt), n, n, n, 0, _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+        self._lib = lib
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pseudo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n = ctypes.c_int64()
+        f = ctypes.c_double()
+        t = ctypes.c_double()
+        check(self._lib.pseudo_info(self._h, ctypes.byref(n), ctypes.byref(f), ctypes.byref(t)))
+        return {"n": n.value, "norm_fro": f.value, "norm2_est": t.value}
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(self._lib.pseudo_stats(self._h, ctypes.byref(s)))
+        return s.as_dict()
+
+    def reset_stats(self):
+        check(self._lib.pseudo_stats_reset(self._h))
+
+    def workspace_bytes(self, npts: int, opts: Opts) -> int:
+        b = ctypes.c_size_t()
+        check(self._lib.pseudo_workspace_bytes(self._h, ctypes.byref(opts), int(npts), ctypes.byref(b)))
+        return b.value
+
+    def grid(self, z, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, **kw):
+        """sigma_min(T - z I) for a 1-D complex128 CUDA tensor (or array) z.
+        Returns dict of CUDA tensors: sigma, res, flags, member, plus 'status'."""
+        torch = _torch()
+        o = opts if opts is not None else default_opts(**kw)
+        zt = torch.as_tensor(np.asarray(z, dtype=np.complex128)) if not torch.is_tensor(z) else z
+        zt = zt.to(device="cuda", dtype=torch.complex128).contiguous()
+        npts = zt.numel()
+        sigma = torch.empty(npts, dtype=torch.float64, device="cuda")
+        res = torch.empty(npts, dtype=torch.float64, device="cuda")
+        flags = torch.empty(npts, dtype=torch.int32, device="cuda")
+        member = torch.zeros(npts, dtype=torch.int32, device="cuda")
+        eps = np.ascontiguousarray(np.asarray(eps_levels, dtype=np.float64))
+        need = self.workspace_bytes(npts, o)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        rc = check(self._lib.pseudo_grid(
+            self._h, _ptr(zt), npts, eps.ctypes.data_as(ctypes.c_void_p) if eps.size else None, int(eps.size),
+            ctypes.byref(o), _ptr(sigma), _ptr(res), _ptr(flags), _ptr(member), _ptr(workspace),
+            workspace.numel(), _stream_ptr(stream)))
+        return {"sigma": sigma, "res": res, "flags": flags, "member": member, "status": rc}
+
+    def grid_host(self, z: np.ndarray, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None,
+                  out=None, **kw):
+        """Same as grid() but z and the outputs are (pinned) host arrays: the
+        library copies them to and from the device inside the call."""
+        torch = _torch()
+        o = opts if opts is not None else default_opts(**kw)
+        o.io_host = 1
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+        npts = z.size
+        if out is None:
+            out = {
+                "sigma": np.empty(npts, np.float64), "res": np.empty(npts, np.float64),
+                "flags": np.empty(npts, np.int32), "member": np.empty(npts, np.uint32),
+            }
+        eps = np.ascontiguousarray(np.asarray(eps_levels, dtype=np.float64))
+        need = self.workspace_bytes(npts, o)
+        if workspace is None or workspace.numel() < need:
+            workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        rc = check(self._lib.pseudo_grid(
+            self._h, vp(z), npts, vp(eps) if eps.size else None, int(eps.size), ctypes.byref(o),
+            vp(out["sigma"]), vp(out["res"]), vp(out["flags"]), vp(out["member"]), _ptr(workspace),
+            workspace.numel(), _stream_ptr(stream)))
+        out["status"] = rc
+        return out
+
+    def solve(self, X, z, adjoint: bool = False, precision: int = FP64, stream=None):
+        """In-place multi-shift triangular solve on a row-major (n, ncols)
+        complex128 CUDA tensor X, column c shifted by z[c]."""
+        torch = _torch()
+        assert X.is_cuda and X.dtype == torch.complex128 and X.is_contiguous() and X.shape[0] == self.n
+        ncols = X.shape[1]
+        zt = torch.as_tensor(z).to(device="cuda", dtype=torch.complex128).contiguous()
+        b = ctypes.c_size_t()
+        check(self._lib.pseudo_solve_workspace_bytes(self._h, ncols, ctypes.byref(b)))
+        ws = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+        check(self._lib.pseudo_solve(self._h, _ptr(X), _ptr(zt), ncols, int(adjoint), int(precision), _ptr(ws),
+                                     b.value, _stream_ptr(stream)))
+        return X
+
+    def matvec(self, X, z=None, B=None, adjoint: bool = False, stream=None):
+        """Y = (T - zI)^{op} X, or B - (T - zI)^{op} X when B is given (FP64)."""
+        torch = _torch()
+        ncols = X.shape[1]
+        Y = torch.empty_like(X)
+        zt = None if z is None else torch.as_tensor(z).to(device="cuda", dtype=torch.complex128).contiguous()
+        check(self._lib.pseudo_matvec(self._h, _ptr(X), _ptr(B), _ptr(Y), _ptr(zt), ncols, int(adjoint),
+                                      int(B is not None), _stream_ptr(stream)))
+        return Y

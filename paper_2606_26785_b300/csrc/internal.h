@@ -1,0 +1,102 @@
+// Launchers shared between the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+#include "pseudo.h"
+
+namespace pseudo {
+
+// tri_kernels.cu
+void launch_pack_panels(const double2 *T, int64_t ldT, int n, int n_pad, double2 *U64, double2 *L64,
+                        float2 *U32, float2 *L32, cudaStream_t s);
+int trsv_group_width(int fp32);
+size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols);
+cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs, cudaStream_t s);
+cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
+cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, const double2 *X, int64_t ldx, const double2 *B,
+                          int64_t ldb, double2 *Y, int64_t ldy, int subtract, cudaStream_t s);
+cudaError_t launch_sumsq(const double2 *a, int64_t cnt, double *out, cudaStream_t s);
+cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, cudaStream_t s);
+
+}  // namespace pseudo
+
+namespace pseudo {
+// lanczos.cu
+constexpr int LANCZOS_MMAX = 64;
+void launch_start_vector(double2 *v, int n, uint64_t seed, cudaStream_t s);
+template <typename real>
+void launch_bcast_start(const double2 *v, int n, int S, cx_t<real> *Q0, cudaStream_t s);
+template <typename real>
+void launch_copy_cols(const cx_t<real> *src, cx_t<real> *dst, int n, int S, const int *active,
+                      cudaStream_t s);
+template <typename real>
+void launch_lanczos_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, int j, int mmax,
+                         const int *active, double *alpha, double *beta, cudaStream_t s);
+void launch_lanczos_tridiag(int S, int j, int mmax, const double *alpha, const double *beta, int *active,
+                            double *theta, double *svec, int *nsteps, double tol_q, double tol_floor, int final_step,
+                            cudaStream_t s);
+void launch_compact_active(const int *active, int S, int *cols, int *cnt, cudaStream_t s);
+template <typename real>
+void launch_ritz_vector(const cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec,
+                        const int *nsteps, double2 *U, const int *mask, cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+// colops.cu
+void launch_colnorm2(const double2 *X, int n, int S, const int *mask, double *out, cudaStream_t s);
+void launch_scale_to32(const double2 *R, int n, int S, const int *mask, const double *rn2, float2 *D, cudaStream_t s);
+void launch_acc_from32(double2 *X, int n, int S, const int *mask, const double *rn2, const float2 *D, cudaStream_t s);
+void launch_normalize(double2 *X, int n, int S, const int *mask, cudaStream_t s);
+void launch_rq_residual(const double2 *U, const double2 *Y, const double2 *NX, int n, int S, const int *mask,
+                        double *s2, double *r, cudaStream_t s);
+void launch_finalize(int S, int64_t w0, const double2 *z, const double *theta, const double *s2, const double *rr,
+                     const int *active, const int *extra_flags, int sig_src, double norm2, const double *eps, int neps,
+                     double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int base_flags,
+                     int *nbad, cudaStream_t s);
+void launch_fill_int(int *a, int n, int v, cudaStream_t s);
+void launch_nonfinite(const double2 *a, int64_t cnt, int *bad, cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+// tsk.cu: batched tall-skinny views. Item b's element (i, j) is p[b*bs + i*ld + j].
+// With map != nullptr item b lives in slot map[b] (e.g. the recycle lane of a
+// refined point).
+// coff != nullptr adds a per-item element offset coff[b] (e.g. the column where
+// a lane's new block starts).
+struct TSView {
+    double2 *p;
+    int64_t ld, bs;
+    const int *map;
+    const int *coff;
+    __host__ __device__ double2 *at(int b) const {
+        return p + (int64_t)(map ? map[b] : b) * bs + (coff ? coff[b] : 0);
+    }
+};
+inline TSView tsv(double2 *p, int64_t ld, int64_t bs, const int *map = nullptr, const int *coff = nullptr) {
+    return TSView{p, ld, bs, map, coff};
+}
+cudaError_t launch_ts_gram(TSView A, int ka, TSView B, int kb, int n, int nitems, const int *items, double2 *G,
+                           int64_t gstride, bool zero, cudaStream_t s);
+cudaError_t launch_ts_mul(TSView A, int ka, const double2 *C, int64_t cstride, TSView O, int kb, int n, int nitems,
+                          const int *items, double beta, double alpha, cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+// recy_update.cu
+void launch_upd_decide(const int *lanes, int nu, int *p, int r, int KM, int p_max, double omega, const double2 *C,
+                       const double2 *gx, int *lout, int *kk, int *nskip, cudaStream_t s);
+void launch_upd_shift(double2 *V, double2 *W1, double2 *W3, double2 *W4, int n, int64_t ld, double2 *H1, double2 *H2,
+                      double2 *Lf, double2 *C, int KM, int r, const int *lanes, int nu, int *p, const int *lout,
+                      cudaStream_t s);
+void launch_upd_chol(const double2 *G, int r, int nu, const int *lout, double2 *R, double2 *Ri, cudaStream_t s);
+void launch_upd_add(double2 *U, const double2 *U2, int cnt, int nu, cudaStream_t s);
+void launch_upd_rotate(double2 *H1, double2 *H2, double2 *Lf, double2 *Qacc, const double2 *U, const double2 *Rnew,
+                       const double2 *Hc1, const double2 *Hc2, const double2 *Hr2, int KM, int r, const int *lanes,
+                       int nu, int *p, const int *kk, cudaStream_t s);
+void launch_small_matmul(const double2 *A, const double2 *B, double2 *C, int m, int nitems, cudaStream_t s);
+void launch_copy_block(TSView src, TSView dst, int n, int kc, int nitems, const int *items, cudaStream_t s);
+}  // namespace pseudo

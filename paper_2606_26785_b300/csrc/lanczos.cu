@@ -1,0 +1,385 @@
+// Shift-batched inverse Lanczos on N(z)^{-1} = (T - zI)^{-1} (T - zI)^{-H}
+// (the EigTool core, Sec. 1): every column c of the batch is one grid point.
+// One Lanczos step for all active columns is
+//     w = (T - z I)^{-1} (T - z I)^{-H} q_j            (two multi-shift solves)
+//     h = Q^H w, w -= Q h  (twice: classical Gram-Schmidt with full
+//                           reorthogonalisation), alpha_j = Re h_j,
+//     beta_j = ||w||, q_{j+1} = w / beta_j,
+// followed by the largest eigenvalue theta of the tridiagonal T_j and the
+// bound beta_j |s_j| on the Ritz residual; sigma = 1/sqrt(theta).
+//
+// Vectors live in row-major n x S arrays (row i of all columns contiguous).
+// Kernels over columns use CTAs of 32 consecutive columns (lane = column,
+// warps split the rows) so that loads are coalesced whatever subset of the
+// columns is still active.
+#include "common.cuh"
+#include "internal.h"
+
+namespace pseudo {
+
+// ------------------------------------------------------- start vector
+// Counter-based generator (SplitMix64 finaliser of seed + i): the start
+// vector is the same for every grid point (no continuation between points).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+__global__ void start_vector_kernel(double2 *v, int n, uint64_t seed) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        uint64_t a = splitmix64(seed * 0x100000001B3ull + 2ull * i);
+        uint64_t b = splitmix64(seed * 0x100000001B3ull + 2ull * i + 1);
+        double re = (double)(a >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        double im = (double)(b >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        v[i] = make_double2(re, im);
+        s += re * re + im * im;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) ws[0] = 1.0 / sqrt(s);
+    }
+    __syncthreads();
+    const double inv = ws[0];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { v[i].x *= inv; v[i].y *= inv; }
+}
+
+template <typename real>
+__global__ void bcast_start_kernel(const double2 *__restrict__ v, int n, int S, cx_t<real> *__restrict__ Q0) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n * S) return;
+    const int i = (int)(idx / S);
+    Q0[idx] = mk<real>((real)v[i].x, (real)v[i].y);
+}
+
+// -------------------------------------------------- copy active columns
+template <typename real>
+__global__ void copy_cols_kernel(const cx_t<real> *__restrict__ src, cx_t<real> *__restrict__ dst, int n, int S,
+                                 const int *__restrict__ active) {
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (c >= S || active[c] != 1) return;
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5) dst[(int64_t)i * S + c] = src[(int64_t)i * S + c];
+}
+
+// --------------------------------------------------- orthogonalisation
+constexpr int ORTH_WARPS = 8, TCH = 8;
+
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+lanczos_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restrict__ W, int n, int S, int j,
+                    int mmax, const int *__restrict__ active, double *__restrict__ alpha,
+                    double *__restrict__ beta) {
+    using C = cx_t<real>;
+    __shared__ double2 red[ORTH_WARPS][TCH][32];
+    __shared__ double2 s_hj[32];
+    __shared__ double s_nrm[ORTH_WARPS][32];
+    __shared__ int any;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool on = (c < S) && active[c] == 1;
+    if (threadIdx.x == 0) any = 0;
+    if (threadIdx.x < 32) s_hj[threadIdx.x] = make_double2(0.0, 0.0);
+    __syncthreads();
+    if (on) any = 1;
+    __syncthreads();
+    if (!any) return;
+    const int cc = on ? c : 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        // h_t = q_t^H w for t = 0..j, in chunks of TCH vectors; then w -= q_t h_t
+        for (int t0 = 0; t0 <= j; t0 += TCH) {
+            double2 acc[TCH];
+#pragma unroll
+            for (int u = 0; u < TCH; ++u) acc[u] = make_double2(0.0, 0.0);
+            if (on) {
+                for (int i = warp; i < n; i += ORTH_WARPS) {
+                    const C wv = W[(int64_t)i * S + cc];
+                    const double wr = wv.x, wi = wv.y;
+#pragma unroll
+                    for (int u = 0; u < TCH; ++u) {
+                        if (t0 + u <= j) {
+                            const C qv = Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc];
+                            acc[u].x += (double)qv.x * wr + (double)qv.y * wi;
+                            acc[u].y += (double)qv.x * wi - (double)qv.y * wr;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TCH; ++u) red[warp][u][lane] = acc[u];
+            __syncthreads();
+            if (warp == 0) {
+                for (int u = 0; u < TCH && t0 + u <= j; ++u) {
+                    double2 s = make_double2(0.0, 0.0);
+                    for (int w = 0; w < ORTH_WARPS; ++w) { s.x += red[w][u][lane].x; s.y += red[w][u][lane].y; }
+                    red[0][u][lane] = s;
+                    if (t0 + u == j) { s_hj[lane].x += s.x; s_hj[lane].y += s.y; }
+                }
+            }
+            __syncthreads();
+            if (on) {
+                double2 hc[TCH];
+#pragma unroll
+                for (int u = 0; u < TCH; ++u) hc[u] = (t0 + u <= j) ? red[0][u][lane] : make_double2(0.0, 0.0);
+                for (int i = warp; i < n; i += ORTH_WARPS) {
+                    C wv = W[(int64_t)i * S + cc];
+                    double wr = wv.x, wi = wv.y;
+#pragma unroll
+                    for (int u = 0; u < TCH; ++u) {
+                        if (t0 + u <= j) {
+                            const C qv = Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc];
+                            wr -= (double)qv.x * hc[u].x - (double)qv.y * hc[u].y;
+                            wi -= (double)qv.x * hc[u].y + (double)qv.y * hc[u].x;
+                        }
+                    }
+                    W[(int64_t)i * S + cc] = mk<real>((real)wr, (real)wi);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // beta = ||w||, q_{j+1} = w / beta
+    double s = 0.0;
+    if (on)
+        for (int i = warp; i < n; i += ORTH_WARPS) {
+            const C wv = W[(int64_t)i * S + cc];
+            s += (double)wv.x * wv.x + (double)wv.y * wv.y;
+        }
+    s_nrm[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ORTH_WARPS; ++w) t += s_nrm[w][lane];
+        s_nrm[0][lane] = sqrt(t);
+    }
+    __syncthreads();
+    const double b = s_nrm[0][lane];
+    if (on) {
+        const double inv = b > 0.0 ? 1.0 / b : 0.0;
+        for (int i = warp; i < n; i += ORTH_WARPS) {
+            const C wv = W[(int64_t)i * S + cc];
+            Q[(int64_t)(j + 1) * qs + (int64_t)i * S + cc] = mk<real>((real)(wv.x * inv), (real)(wv.y * inv));
+        }
+        if (warp == 0) {
+            alpha[(int64_t)c * mmax + j] = s_hj[lane].x;
+            beta[(int64_t)c * mmax + j] = b;
+        }
+    }
+}
+
+// ------------------------------------------------ tridiagonal eigen
+// Sturm count: number of eigenvalues of the k x k symmetric tridiagonal
+// (a, b) that are < x.
+__device__ int sturm_count(const double *a, const double *b, int k, double x, double pivmin) {
+    int cnt = 0;
+    double d = a[0] - x;
+    if (fabs(d) < pivmin) d = -pivmin;
+    if (d < 0) cnt++;
+    for (int i = 1; i < k; ++i) {
+        d = a[i] - x - b[i - 1] * b[i - 1] / d;
+        if (fabs(d) < pivmin) d = -pivmin;
+        if (d < 0) cnt++;
+    }
+    return cnt;
+}
+
+// eigenvalue number `idx` (0 = smallest) by bisection
+__device__ double tridiag_eig(const double *a, const double *b, int k, int idx) {
+    double lo = a[0], hi = a[0], bmax = 0.0;
+    for (int i = 0; i < k; ++i) {
+        double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+        if (i < k - 1) bmax = fmax(bmax, fabs(b[i]));
+    }
+    const double scale = fmax(fabs(lo), fabs(hi));
+    const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * scale * scale + 2.2250738585072014e-308);
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(a, b, k, mid, pivmin) > idx) hi = mid; else lo = mid;
+        if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Eigenvector of the tridiagonal for eigenvalue lam by two steps of inverse
+// iteration (tridiagonal LU with partial pivoting); result normalised.
+__device__ void tridiag_vec(const double *a, const double *b, int k, double lam, double *s, double *wk) {
+    // wk layout: d (k), du (k), du2 (k), dl (k), piv as double (k)
+    double *d = wk, *du = wk + k, *du2 = wk + 2 * k, *dl = wk + 3 * k, *pv = wk + 4 * k;
+    const double tiny = 1e-300 + 1e-15 * fabs(lam);
+    for (int i = 0; i < k; ++i) { s[i] = 1.0; }
+    for (int rep = 0; rep < 2; ++rep) {
+        for (int i = 0; i < k; ++i) { d[i] = a[i] - lam; du[i] = i < k - 1 ? b[i] : 0.0; dl[i] = i < k - 1 ? b[i] : 0.0; du2[i] = 0.0; pv[i] = 0.0; }
+        for (int i = 0; i < k - 1; ++i) {
+            if (fabs(d[i]) >= fabs(dl[i])) {
+                if (fabs(d[i]) < tiny) d[i] = tiny;
+                double f = dl[i] / d[i];
+                dl[i] = f;
+                d[i + 1] -= f * du[i];
+                pv[i] = 0.0;
+            } else {
+                double f = d[i] / dl[i];
+                d[i] = dl[i];
+                dl[i] = f;
+                double tmp = du[i];
+                du[i] = d[i + 1];
+                d[i + 1] = tmp - f * d[i + 1];
+                if (i < k - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+                pv[i] = 1.0;
+            }
+        }
+        if (fabs(d[k - 1]) < tiny) d[k - 1] = tiny;
+        // forward: apply L^{-1} P
+        for (int i = 0; i < k - 1; ++i) {
+            if (pv[i] != 0.0) { double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - dl[i] * s[i]; }
+            else s[i + 1] -= dl[i] * s[i];
+        }
+        // backward: U^{-1}
+        s[k - 1] /= d[k - 1];
+        if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / d[k - 2];
+        for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / d[i];
+        double nr = 0.0;
+        for (int i = 0; i < k; ++i) nr += s[i] * s[i];
+        nr = 1.0 / sqrt(nr);
+        for (int i = 0; i < k; ++i) s[i] *= nr;
+    }
+}
+
+// For every active column after step j: theta_max, gap and convergence.
+__global__ void lanczos_tridiag_kernel(int S, int j, int mmax, const double *__restrict__ alpha,
+                                       const double *__restrict__ beta, int *__restrict__ active,
+                                       double *__restrict__ theta, double *__restrict__ svec,
+                                       int *__restrict__ nsteps, double tol_q, double tol_floor,
+                                       int final_step) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S || !active[c]) return;
+    const int k = j + 1;
+    double a[LANCZOS_MMAX], b[LANCZOS_MMAX], s[LANCZOS_MMAX], wk[5 * LANCZOS_MMAX];
+    for (int i = 0; i < k; ++i) { a[i] = alpha[(int64_t)c * mmax + i]; b[i] = beta[(int64_t)c * mmax + i]; }
+    const double th1 = tridiag_eig(a, b, k, k - 1);
+    const double th2 = k > 1 ? tridiag_eig(a, b, k, k - 2) : 0.0;
+    tridiag_vec(a, b, k, th1, s, wk);
+    const double rb = fabs(b[k - 1] * s[k - 1]);  // ||N^{-1} u - theta u||
+    const double gap = fmax(th1 - th2, 1e-300);
+    const double est = rb * rb / (th1 * gap);     // relative error bound on theta
+    const bool breakdown = b[k - 1] <= 1e-300 * th1;
+    const bool conv = breakdown || est <= tol_q || rb <= tol_floor * th1;
+    theta[c] = th1;
+    nsteps[c] = k;
+    for (int i = 0; i < k; ++i) svec[(int64_t)c * mmax + i] = s[i];
+    if (conv || final_step) active[c] = conv ? 0 : -1;  // -1: stopped unconverged
+}
+
+// Active list: cols[] = indices with active[c] == 1, count in *cnt.  One CTA.
+__global__ void compact_active_kernel(const int *__restrict__ active, int S, int *__restrict__ cols, int *cnt) {
+    __shared__ int base;
+    __shared__ int wsum[32];
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < S; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const int f = (c < S && active[c] == 1) ? 1 : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { int t = wsum[w]; wsum[w] = acc; acc += t; }
+        }
+        __syncthreads();
+        if (f) cols[base + wsum[warp] + __popc(m & ((1u << lane) - 1u))] = c;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base += wsum[warp] + __popc(m);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *cnt = base;
+}
+
+// Ritz vector u_c = sum_t s_t q_t (FP64 out), normalised.
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+ritz_vector_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, int mmax,
+                   const double *__restrict__ svec, const int *__restrict__ nsteps, double2 *__restrict__ U,
+                   const int *__restrict__ mask) {
+    __shared__ double s_nrm[ORTH_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool on = c < S && (mask == nullptr || mask[c]);
+    const int k = on ? nsteps[c] : 0;
+    double s = 0.0;
+    for (int i = warp; i < n; i += ORTH_WARPS) {
+        if (!on) break;
+        double ur = 0.0, ui = 0.0;
+        for (int t = 0; t < k; ++t) {
+            const double st = svec[(int64_t)c * mmax + t];
+            const cx_t<real> qv = Q[(int64_t)t * qs + (int64_t)i * S + c];
+            ur += st * qv.x; ui += st * qv.y;
+        }
+        U[(int64_t)i * S + c] = make_double2(ur, ui);
+        s += ur * ur + ui * ui;
+    }
+    s_nrm[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ORTH_WARPS; ++w) t += s_nrm[w][lane];
+        s_nrm[0][lane] = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_nrm[0][lane];
+    if (on)
+        for (int i = warp; i < n; i += ORTH_WARPS) { double2 v = U[(int64_t)i * S + c]; v.x *= inv; v.y *= inv; U[(int64_t)i * S + c] = v; }
+}
+
+// ------------------------------------------------------------ launchers
+void launch_start_vector(double2 *v, int n, uint64_t seed, cudaStream_t s) {
+    start_vector_kernel<<<1, 1024, 0, s>>>(v, n, seed);
+}
+template <typename real>
+void launch_bcast_start(const double2 *v, int n, int S, cx_t<real> *Q0, cudaStream_t s) {
+    int64_t tot = (int64_t)n * S;
+    bcast_start_kernel<real><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(v, n, S, Q0);
+}
+template <typename real>
+void launch_copy_cols(const cx_t<real> *src, cx_t<real> *dst, int n, int S, const int *active, cudaStream_t s) {
+    copy_cols_kernel<real><<<(S + 31) / 32, 256, 0, s>>>(src, dst, n, S, active);
+}
+template <typename real>
+void launch_lanczos_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, int j, int mmax, const int *active,
+                         double *alpha, double *beta, cudaStream_t s) {
+    lanczos_orth_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, j, mmax, active, alpha, beta);
+}
+void launch_lanczos_tridiag(int S, int j, int mmax, const double *alpha, const double *beta, int *active,
+                            double *theta, double *svec, int *nsteps, double tol_q, double tol_floor, int final_step,
+                            cudaStream_t s) {
+    lanczos_tridiag_kernel<<<(S + 63) / 64, 64, 0, s>>>(S, j, mmax, alpha, beta, active, theta, svec, nsteps, tol_q,
+                                                        tol_floor, final_step);
+}
+void launch_compact_active(const int *active, int S, int *cols, int *cnt, cudaStream_t s) {
+    compact_active_kernel<<<1, 1024, 0, s>>>(active, S, cols, cnt);
+}
+template <typename real>
+void launch_ritz_vector(const cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, const int *nsteps,
+                        double2 *U, const int *mask, cudaStream_t s) {
+    ritz_vector_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, n, S, mmax, svec, nsteps, U, mask);
+}
+
+template void launch_bcast_start<float>(const double2 *, int, int, float2 *, cudaStream_t);
+template void launch_bcast_start<double>(const double2 *, int, int, double2 *, cudaStream_t);
+template void launch_copy_cols<float>(const float2 *, float2 *, int, int, const int *, cudaStream_t);
+template void launch_copy_cols<double>(const double2 *, double2 *, int, int, const int *, cudaStream_t);
+template void launch_lanczos_orth<float>(float2 *, int64_t, float2 *, int, int, int, int, const int *, double *, double *, cudaStream_t);
+template void launch_lanczos_orth<double>(double2 *, int64_t, double2 *, int, int, int, int, const int *, double *, double *, cudaStream_t);
+template void launch_ritz_vector<float>(const float2 *, int64_t, int, int, int, const double *, const int *, double2 *, const int *, cudaStream_t);
+template void launch_ritz_vector<double>(const double2 *, int64_t, int, int, int, const double *, const int *, double2 *, const int *, cudaStream_t);
+
+}  // namespace pseudo

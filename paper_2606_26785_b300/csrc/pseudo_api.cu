@@ -1,0 +1,310 @@
+// Host side of the C ABI declared in include/pseudo.h: handle set-up (packed
+// panels of T, norms), argument checking, workspace carving, and the grid
+// drivers (inverse Lanczos here; recycling in recycle_driver.cu).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "pseudo.h"
+#include "driver.h"
+
+namespace pseudo {
+
+static thread_local std::string g_err;
+
+int set_err(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+void clear_err() { g_err.clear(); }
+
+int cuda_err(cudaError_t e, const char *where) {
+    return set_err(PSEUDO_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------- workspace
+void *Carver::take(size_t bytes) {
+    size_t off = (used + 255) & ~(size_t)255;
+    used = off + bytes;
+    if (!base || used > cap) { overflow = true; return nullptr; }
+    return base + off;
+}
+
+}  // namespace pseudo
+
+using namespace pseudo;
+
+extern "C" {
+
+const char *pseudo_last_error(void) { return g_err.c_str(); }
+
+int pseudo_opts_default(pseudo_opts *o) {
+    if (!o) return set_err(PSEUDO_ERR_ARG, "opts is NULL");
+    memset(o, 0, sizeof *o);
+    o->mode = PSEUDO_INVLANC;
+    o->precision = PSEUDO_FP64;
+    o->r = 6;
+    o->p_max = 60;
+    o->batch_b = 20;
+    o->eps_shift_rel = 1e-14;
+    o->tau = 1e-10;
+    o->omega = 1.6;
+    o->eta = 1e-4;
+    o->rtol = 1e-10;
+    o->maxiter_lanczos = 64;
+    o->maxiter_lobpcg = 60;
+    o->max_ir = 4;
+    o->seed = 12345;
+    return PSEUDO_OK;
+}
+
+int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_on_host, void *stream,
+                  pseudo_handle *out) {
+    clear_err();
+    if (!out) return set_err(PSEUDO_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!T) return set_err(PSEUDO_ERR_ARG, "T is NULL");
+    if (m != n) return set_err(PSEUDO_ERR_UNSUPPORTED, "rectangular input (m=%lld, n=%lld) is not supported", (long long)m, (long long)n);
+    if (n < 1 || n > (1 << 20)) return set_err(PSEUDO_ERR_ARG, "n=%lld out of range", (long long)n);
+    if (ldT < n) return set_err(PSEUDO_ERR_ARG, "ldT=%lld < n=%lld", (long long)ldT, (long long)n);
+    cudaStream_t s = (cudaStream_t)stream;
+    pseudo_ctx *h = new pseudo_ctx();
+    h->n = (int)n;
+    h->n_pad = (int)((n + PH - 1) / PH * PH);
+    cudaGetDevice(&h->dev);
+    const int64_t psz = packed_size(h->n_pad);
+    cudaError_t e;
+    double2 *Td = nullptr;
+    int *bad = nullptr;
+    double *dsum = nullptr;
+    auto fail = [&](int code) {
+        if (Td && t_on_host) cudaFree(Td);
+        if (bad) cudaFree(bad);
+        if (dsum) cudaFree(dsum);
+        pseudo_destroy(h);
+        return code;
+    };
+    if ((e = cudaMalloc(&h->U64, psz * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc U64"));
+    if ((e = cudaMalloc(&h->L64, psz * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L64"));
+    if ((e = cudaMalloc(&h->U32, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc U32"));
+    if ((e = cudaMalloc(&h->L32, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L32"));
+    if ((e = cudaMalloc(&h->diag, n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc diag"));
+    if ((e = cudaMalloc(&bad, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
+    if ((e = cudaMalloc(&dsum, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
+    if (t_on_host) {
+        if ((e = cudaMalloc(&Td, (size_t)ldT * n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc T"));
+        if ((e = cudaMemcpyAsync(Td, T, (size_t)ldT * n * sizeof(double2), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return fail(cuda_err(e, "copy T"));
+    } else {
+        Td = (double2 *)T;
+    }
+    launch_pack_panels(Td, ldT, (int)n, h->n_pad, h->U64, h->L64, h->U32, h->L32, s);
+    cudaMemsetAsync(bad, 0, sizeof(int), s);
+    launch_nonfinite(h->U64, psz, bad, s);
+    launch_extract_diag(h->U64, (int)n, h->n_pad, h->diag, s);
+    launch_sumsq(h->U64, psz, dsum, s);
+    int hbad = 0;
+    double fro2 = 0.0;
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&fro2, dsum, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_err(e, "pack T"));
+    if (hbad) return fail(set_err(PSEUDO_ERR_NONFINITE, "T has non-finite entries in its upper triangle"));
+    h->norm_fro = sqrt(fro2);
+    // ||T||_2 estimate: power iteration on T^H T from a seeded vector
+    {
+        double2 *x = nullptr, *y = nullptr;
+        if ((e = cudaMalloc(&x, n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
+        if ((e = cudaMalloc(&y, n * sizeof(double2))) != cudaSuccess) { cudaFree(x); return fail(cuda_err(e, "cudaMalloc")); }
+        launch_start_vector(x, (int)n, 99, s);
+        double lam = 0.0;
+        for (int it = 0; it < 30; ++it) {
+            launch_trmv64(h->U64, (int)n, h->n_pad, 0, nullptr, nullptr, 1, nullptr, x, 1, nullptr, 1, y, 1, 0, s);
+            launch_trmv64(h->L64, (int)n, h->n_pad, 1, nullptr, nullptr, 1, nullptr, y, 1, nullptr, 1, x, 1, 0, s);
+            launch_colnorm2(x, (int)n, 1, nullptr, dsum, s);
+            double nx2 = 0.0;
+            cudaMemcpyAsync(&nx2, dsum, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            lam = sqrt(nx2);  // ||T^H T x|| for unit x
+            if (!(lam > 0.0)) break;
+            launch_normalize(x, (int)n, 1, nullptr, s);
+        }
+        cudaFree(x);
+        cudaFree(y);
+        h->norm2 = lam > 0.0 ? sqrt(lam) : h->norm_fro;
+        if (h->norm2 > h->norm_fro) h->norm2 = h->norm_fro;
+    }
+    if (t_on_host) cudaFree(Td);
+    Td = nullptr;
+    cudaFree(bad); bad = nullptr;
+    cudaFree(dsum); dsum = nullptr;
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(e, "create"));
+    memset(&h->stats, 0, sizeof h->stats);
+    *out = h;
+    return PSEUDO_OK;
+}
+
+void pseudo_destroy(pseudo_handle h) {
+    if (!h) return;
+    cudaFree(h->U64);
+    cudaFree(h->L64);
+    cudaFree(h->U32);
+    cudaFree(h->L32);
+    cudaFree(h->diag);
+    delete h;
+}
+
+int pseudo_info(pseudo_handle h, int64_t *n, double *norm_fro, double *norm2_est) {
+    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
+    if (n) *n = h->n;
+    if (norm_fro) *norm_fro = h->norm_fro;
+    if (norm2_est) *norm2_est = h->norm2;
+    return PSEUDO_OK;
+}
+
+int pseudo_stats(pseudo_handle h, pseudo_stats_t *out) {
+    if (!h || !out) return set_err(PSEUDO_ERR_ARG, "NULL argument");
+    *out = h->stats;
+    return PSEUDO_OK;
+}
+
+int pseudo_stats_reset(pseudo_handle h) {
+    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
+    memset(&h->stats, 0, sizeof h->stats);
+    return PSEUDO_OK;
+}
+
+int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) {
+    if (!h || !bytes || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    Carver c;
+    c.take(trsv_scratch_bytes(1, h->n_pad, ncols));
+    c.take((size_t)h->n * ncols * sizeof(float2));
+    c.take(trsv_scratch_bytes(0, h->n_pad, ncols));
+    *bytes = c.used + 256;
+    return PSEUDO_OK;
+}
+
+int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint, int precision,
+                 void *workspace, size_t workspace_bytes, void *stream) {
+    clear_err();
+    if (!h || !X || !z || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED) return set_err(PSEUDO_ERR_ARG, "bad precision");
+    if (ncols == 0) return PSEUDO_OK;
+    size_t need = 0;
+    pseudo_solve_workspace_bytes(h, ncols, &need);
+    if (!workspace || workspace_bytes < need) return set_err(PSEUDO_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c((char *)workspace, workspace_bytes);
+    const int lower = adjoint ? 1 : 0;
+    cudaError_t e;
+    if (precision == PSEUDO_FP64) {
+        double2 *xs = (double2 *)c.take(trsv_scratch_bytes(0, h->n_pad, ncols));
+        e = launch_trsv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
+                          nullptr, (double2 *)X, ncols, xs, s);
+    } else {
+        float2 *xs = (float2 *)c.take(trsv_scratch_bytes(1, h->n_pad, ncols));
+        float2 *X32 = (float2 *)c.take((size_t)h->n * ncols * sizeof(float2));
+        launch_convert_64_to_32((const double2 *)X, X32, (int64_t)h->n * ncols, s);
+        e = launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
+                          nullptr, X32, ncols, xs, s);
+        launch_convert_32_to_64(X32, (double2 *)X, (int64_t)h->n * ncols, s);
+    }
+    if (e != cudaSuccess) return cuda_err(e, "pseudo_solve");
+    h->stats.sv_R += ncols;
+    return PSEUDO_OK;
+}
+
+int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y, const pseudo_c64 *z,
+                  int64_t ncols, int adjoint, int subtract, void *stream) {
+    clear_err();
+    if (!h || !X || !Y || ncols < 0 || (subtract && !B)) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if ((const void *)X == (const void *)Y) return set_err(PSEUDO_ERR_ARG, "Y must not alias X");
+    if (ncols == 0) return PSEUDO_OK;
+    const int lower = adjoint ? 1 : 0;
+    cudaError_t e = launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z,
+                                  (int)ncols, nullptr, (const double2 *)X, ncols, (const double2 *)B, ncols,
+                                  (double2 *)Y, ncols, subtract, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_err(e, "pseudo_matvec");
+    h->stats.mv_M += ncols;
+    return PSEUDO_OK;
+}
+
+static int check_opts(const pseudo_opts *o) {
+    if (!o) return set_err(PSEUDO_ERR_ARG, "opts is NULL");
+    if (o->mode != PSEUDO_INVLANC && o->mode != PSEUDO_RECYCLE) return set_err(PSEUDO_ERR_ARG, "bad mode %d", o->mode);
+    if (o->precision != PSEUDO_FP64 && o->precision != PSEUDO_MIXED) return set_err(PSEUDO_ERR_ARG, "bad precision");
+    if (o->maxiter_lanczos < 1 || o->maxiter_lanczos > LANCZOS_MMAX)
+        return set_err(PSEUDO_ERR_ARG, "maxiter_lanczos must be in [1, %d]", LANCZOS_MMAX);
+    if (o->max_ir < 1 || o->max_ir > 32) return set_err(PSEUDO_ERR_ARG, "max_ir must be in [1, 32]");
+    if (o->shift_batch < 0) return set_err(PSEUDO_ERR_ARG, "shift_batch < 0");
+    if (!(o->rtol >= 0.0)) return set_err(PSEUDO_ERR_ARG, "rtol < 0");
+    if (o->mode == PSEUDO_RECYCLE) {
+        if (o->r < 1 || o->r > 8) return set_err(PSEUDO_ERR_ARG, "r must be in [1, 8]");
+        if (o->p_max < 1) return set_err(PSEUDO_ERR_ARG, "p_max must be >= 1");
+        if (!(o->omega >= 1.0)) return set_err(PSEUDO_ERR_ARG, "omega must be >= 1");
+        if (o->batch_b < 1) return set_err(PSEUDO_ERR_ARG, "batch_b must be >= 1");
+        if (o->grid_nx < 0 || o->grid_ny < 0) return set_err(PSEUDO_ERR_ARG, "bad grid dims");
+    }
+    return PSEUDO_OK;
+}
+
+int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, size_t *bytes) {
+    clear_err();
+    if (!h || !bytes || npts < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    Carver c;
+    if (o->mode == PSEUDO_INVLANC) invlanc_carve(h, o, npts, c, nullptr);
+    else recycle_carve(h, o, npts, c, nullptr);
+    *bytes = c.used + 256;
+    return PSEUDO_OK;
+}
+
+int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double *eps_levels, int neps,
+                const pseudo_opts *o, double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out,
+                void *workspace, size_t workspace_bytes, void *stream) {
+    clear_err();
+    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
+    int rc = check_opts(o);
+    if (rc) return rc;
+    if (npts < 0 || npts > (int64_t)1 << 31) return set_err(PSEUDO_ERR_ARG, "npts out of range");
+    if (npts == 0) return PSEUDO_OK;
+    if (!z || !sigma_out) return set_err(PSEUDO_ERR_ARG, "z and sigma_out are required");
+    if (neps < 0 || neps > 32 || (neps > 0 && !eps_levels)) return set_err(PSEUDO_ERR_ARG, "bad eps levels");
+    if (o->mode == PSEUDO_RECYCLE && o->grid_nx > 0 && (int64_t)o->grid_nx * o->grid_ny != npts)
+        return set_err(PSEUDO_ERR_ARG, "grid_nx * grid_ny != npts");
+    if (o->io_host) {
+        for (int64_t i = 0; i < npts; ++i)
+            if (!std::isfinite(z[i].re) || !std::isfinite(z[i].im)) return set_err(PSEUDO_ERR_NONFINITE, "z[%lld] is not finite", (long long)i);
+    }
+    size_t need = 0;
+    pseudo_workspace_bytes(h, o, npts, &need);
+    if (!workspace || workspace_bytes < need)
+        return set_err(PSEUDO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, need);
+    if (((uintptr_t)workspace) & 255) return set_err(PSEUDO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    GridIO io;
+    io.z = (const double2 *)z;
+    io.npts = npts;
+    io.eps_host = eps_levels;
+    io.neps = neps;
+    io.sigma = sigma_out;
+    io.res = res_out;
+    io.flags = flags_out;
+    io.member = member_out;
+    io.on_host = o->io_host != 0;
+    Carver c((char *)workspace, workspace_bytes);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o->mode == PSEUDO_INVLANC) return invlanc_run(h, o, io, c, s);
+    return recycle_run(h, o, io, c, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,357 @@
+// Multi-shift triangular kernels on the packed panels of T.
+//
+//  * pack_panels       : T (column-major FP64) -> upper panels of T and lower
+//                        panels of T^H, in FP64 and FP32.
+//  * trsv_ms           : (T - z_c I) x_c = b_c  or  (T - z_c I)^H x_c = b_c for
+//                        many columns c at once, each with its own shift: the
+//                        R(z)^{-1} / R(z)^{-*} applications of Alg. 3 and of the
+//                        inverse-Lanczos comparator (sv_R in Table 2).
+//  * trmv_ms (FP64)    : y_c = b_c - (T - z_c I)^{op} x_c  (or without b): the
+//                        refinement residual and the products T V, T^H V of
+//                        Alg. 2 (mv_M in Table 2).
+//
+// Blocking: a CTA owns R right-hand sides.  Row panels of 64 rows are solved
+// one after another (bottom-up for T, top-down for T^H).  For a panel, the
+// off-diagonal contribution sum_K T_IK x_K is split over the CTA's warps (lane
+// l of a warp holds rows l and l+32 of the panel, R accumulators each), summed
+// through shared memory, and warp 0 then solves the 64 x 64 diagonal block
+// with warp shuffles.  Solutions already computed are read from a compact
+// per-CTA copy (scratch: 64-row-padded n x R per CTA), so every x_k load is a
+// contiguous broadcast of R values.
+#include "common.cuh"
+#include "internal.h"
+
+namespace pseudo {
+
+template <typename real> __device__ __forceinline__ cx_t<real> cvt(double2 v);
+template <> __device__ __forceinline__ double2 cvt<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt<float>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+template <typename real>
+__global__ void pack_panels_kernel(const double2 *__restrict__ T, int64_t ldT, int n, int n_pad,
+                                   cx_t<real> *__restrict__ U, cx_t<real> *__restrict__ L) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_pad * n_pad) return;
+    const int k = (int)(idx / n_pad), i = (int)(idx % n_pad);
+    const int P = i / PH, li = i % PH;
+    if (k >= P * PH) {  // row i of T, column k (upper triangle only)
+        double2 v = (i < n && k < n && i <= k) ? T[(int64_t)k * ldT + i] : make_double2(0.0, 0.0);
+        int64_t rel = k - (int64_t)P * PH;
+        U[upper_panel_offset(P, n_pad) + (rel >> 1) * (2 * PH) + 2 * li + (rel & 1)] = cvt<real>(v);
+    }
+    if (k < (P + 1) * PH) {  // row i of T^H, column k: conj(T(k, i)) for k <= i
+        double2 v = (i < n && k < n && k <= i) ? T[(int64_t)i * ldT + k] : make_double2(0.0, 0.0);
+        v.y = -v.y;
+        L[lower_panel_offset(P) + (int64_t)(k >> 1) * (2 * PH) + 2 * li + (k & 1)] = cvt<real>(v);
+    }
+}
+
+void launch_pack_panels(const double2 *T, int64_t ldT, int n, int n_pad, double2 *U64, double2 *L64,
+                        float2 *U32, float2 *L32, cudaStream_t s) {
+    int64_t tot = (int64_t)n_pad * n_pad;
+    int th = 256;
+    int64_t bl = (tot + th - 1) / th;
+    pack_panels_kernel<double><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U64, L64);
+    pack_panels_kernel<float><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U32, L32);
+}
+
+// ------------------------------------------------------------------ solve
+template <typename real, int R, int NW>
+__global__ void __launch_bounds__(NW * 32)
+trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
+               const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
+               const int *__restrict__ ncols_dev, cx_t<real> *X, int64_t ldx, cx_t<real> *xs_all) {
+    using C = cx_t<real>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *red = reinterpret_cast<C *>(smem_raw);   // [NW][PH][R]
+    C *s_dinv = red + NW * PH * R;               // [PH][R]
+    __shared__ int s_col[R];
+    __shared__ double2 s_z[R];
+
+    const int ncols = ncols_dev ? *ncols_dev : ncols_host;
+    const int g = blockIdx.x;
+    if (g * R >= ncols) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < R) {
+        int pos = g * R + threadIdx.x;
+        int c = -1;
+        double2 z = make_double2(0.0, 0.0);
+        if (pos < ncols) { c = cols ? cols[pos] : pos; z = zc[c]; }
+        if (lower) z.y = -z.y;  // (T - zI)^H = T^H - conj(z) I
+        s_col[threadIdx.x] = c;
+        s_z[threadIdx.x] = z;
+    }
+    __syncthreads();
+    C *xs = xs_all + (int64_t)g * n_pad * R;
+    const int npan = n_pad / PH;
+
+    for (int step = 0; step < npan; ++step) {
+        const int P = lower ? step : npan - 1 - step;
+        const C *pan = Pn + (lower ? lower_panel_offset(P) : upper_panel_offset(P, n_pad));
+        int kp0, kp1, kcol0;
+        if (!lower) { kp0 = PH / 2; kp1 = (n_pad - P * PH) / 2; kcol0 = P * PH; }
+        else { kp0 = 0; kp1 = P * PH / 2; kcol0 = 0; }
+
+        C acc[2][R];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = 0; c < R; ++c) acc[q][c] = mk<real>(0, 0);
+
+        const int nk = kp1 - kp0;
+        const int per = (nk + NW - 1) / NW;
+        const int a = kp0 + warp * per;
+        const int b = min(kp1, a + per);
+#pragma unroll 2
+        for (int kp = a; kp < b; ++kp) {
+            const C *tp = pan + (int64_t)kp * (2 * PH) + 2 * lane;
+            const C t00 = tp[0], t01 = tp[1], t10 = tp[64], t11 = tp[65];
+            const C *x0 = xs + (int64_t)(kcol0 + 2 * kp) * R;
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                const C xa = x0[c], xb = x0[R + c];
+                cfma(acc[0][c], t00, xa); cfma(acc[0][c], t01, xb);
+                cfma(acc[1][c], t10, xa); cfma(acc[1][c], t11, xb);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = 0; c < R; ++c) red[((warp * PH) + lane + 32 * q) * R + c] = acc[q][c];
+        // inverse diagonal of this panel for every column
+        for (int e = threadIdx.x; e < PH * R; e += NW * 32) {
+            const int li = e / R, c = e % R, row = P * PH + li;
+            C d = mk<real>(0, 0);
+            if (row < n) {
+                const int64_t dp = lower ? (int64_t)(P * 32 + (li >> 1)) : (int64_t)(li >> 1);
+                const C t = pan[dp * (2 * PH) + 2 * li + (li & 1)];
+                double2 dd = make_double2((double)t.x - s_z[c].x, (double)t.y - s_z[c].y);
+                dd = crecip(dd);
+                d = mk<real>((real)dd.x, (real)dd.y);
+            }
+            s_dinv[li * R + c] = d;
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            C tot[2][R];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int row = P * PH + lane + 32 * q;
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
+                    C bv = mk<real>(0, 0);
+                    if (row < n && s_col[c] >= 0) bv = X[(int64_t)row * ldx + s_col[c]];
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) bv = csub(bv, red[((w * PH) + lane + 32 * q) * R + c]);
+                    tot[q][c] = bv;
+                }
+            }
+            if (!lower) {
+#pragma unroll
+                for (int q = 1; q >= 0; --q) {
+                    for (int l = 31; l >= 0; --l) {
+                        const int i = 32 * q + l;
+                        const C *dcol = pan + (int64_t)(i >> 1) * (2 * PH) + (i & 1);
+                        const C t0 = dcol[2 * lane], t1 = dcol[2 * (lane + 32)];
+#pragma unroll
+                        for (int c = 0; c < R; ++c) {
+                            C xi = shfl_c(cmul(tot[q][c], s_dinv[i * R + c]), l);
+                            if (lane == l) tot[q][c] = xi;
+                            if (q == 1) {
+                                cfms(tot[0][c], t0, xi);
+                                if (lane < l) cfms(tot[1][c], t1, xi);
+                            } else {
+                                if (lane < l) cfms(tot[0][c], t0, xi);
+                            }
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    for (int l = 0; l < 32; ++l) {
+                        const int i = 32 * q + l;
+                        const C *dcol = pan + (int64_t)(P * 32 + (i >> 1)) * (2 * PH) + (i & 1);
+                        const C t0 = dcol[2 * lane], t1 = dcol[2 * (lane + 32)];
+#pragma unroll
+                        for (int c = 0; c < R; ++c) {
+                            C xi = shfl_c(cmul(tot[q][c], s_dinv[i * R + c]), l);
+                            if (lane == l) tot[q][c] = xi;
+                            if (q == 0) {
+                                if (lane > l) cfms(tot[0][c], t0, xi);
+                                cfms(tot[1][c], t1, xi);
+                            } else {
+                                if (lane > l) cfms(tot[1][c], t1, xi);
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int row = P * PH + lane + 32 * q;
+#pragma unroll
+                for (int c = 0; c < R; ++c) {
+                    const C v = row < n ? tot[q][c] : mk<real>(0, 0);
+                    xs[(int64_t)row * R + c] = v;
+                    if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename real, int R, int NW>
+static size_t trsv_smem() { return sizeof(cx_t<real>) * (size_t)(NW * PH * R + PH * R); }
+
+template <typename real, int R, int NW>
+static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower, const int *cols,
+                               const double2 *zc, int ncols, const int *ncols_dev, cx_t<real> *X,
+                               int64_t ldx, cx_t<real> *xs, cudaStream_t s) {
+    size_t sm = trsv_smem<real, R, NW>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(trsv_ms_kernel<real, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    int grid = (ncols + R - 1) / R;
+    if (grid == 0) return cudaSuccess;
+    trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs);
+    return cudaGetLastError();
+}
+
+// Column-group width of the solves: FP64 8 columns, FP32 16 columns per CTA.
+constexpr int R64 = 8, R32 = 16, NW_SOLVE = 8;
+int trsv_group_width(int fp32) { return fp32 ? R32 : R64; }
+
+size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols) {
+    int R = fp32 ? R32 : R64;
+    int64_t groups = (ncols + R - 1) / R;
+    return (size_t)groups * n_pad * R * (fp32 ? sizeof(float2) : sizeof(double2));
+}
+
+cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs, cudaStream_t s) {
+    return trsv_launch<double, R64, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+}
+cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
+    return trsv_launch<float, R32, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+}
+
+// ----------------------------------------------------------------- matvec
+template <int R, int NW>
+__global__ void __launch_bounds__(NW * 32)
+trmv_ms_kernel(const double2 *__restrict__ Pn, int n, int n_pad, int lower, const int *__restrict__ cols,
+               const double2 *__restrict__ zc, int ncols_host, const int *__restrict__ ncols_dev,
+               const double2 *__restrict__ X, int64_t ldx, const double2 *__restrict__ B, int64_t ldb,
+               double2 *__restrict__ Y, int64_t ldy, int subtract) {
+    using C = double2;
+    __shared__ C red[NW][PH][R];
+    __shared__ int s_col[R];
+    __shared__ double2 s_z[R];
+    const int ncols = ncols_dev ? *ncols_dev : ncols_host;
+    const int P = blockIdx.x, g = blockIdx.y;
+    if (g * R >= ncols) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < R) {
+        int pos = g * R + threadIdx.x;
+        int c = -1;
+        double2 z = make_double2(0.0, 0.0);
+        if (pos < ncols) { c = cols ? cols[pos] : pos; if (zc) z = zc[c]; }
+        if (lower) z.y = -z.y;
+        s_col[threadIdx.x] = c;
+        s_z[threadIdx.x] = z;
+    }
+    __syncthreads();
+    const C *pan = Pn + (lower ? lower_panel_offset(P) : upper_panel_offset(P, n_pad));
+    const int kp1 = lower ? (P + 1) * PH / 2 : (n_pad - P * PH) / 2;
+    const int kcol0 = lower ? 0 : P * PH;
+    C acc[2][R];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < R; ++c) acc[q][c] = make_double2(0.0, 0.0);
+    const int per = (kp1 + NW - 1) / NW;
+    const int a = warp * per, b = min(kp1, a + per);
+    for (int kp = a; kp < b; ++kp) {
+        const C *tp = pan + (int64_t)kp * (2 * PH) + 2 * lane;
+        const C t00 = tp[0], t01 = tp[1], t10 = tp[64], t11 = tp[65];
+        const int k0 = kcol0 + 2 * kp;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            const int cc = s_col[c];
+            C xa = make_double2(0.0, 0.0), xb = xa;
+            if (cc >= 0) {
+                if (k0 < n) xa = X[(int64_t)k0 * ldx + cc];
+                if (k0 + 1 < n) xb = X[(int64_t)(k0 + 1) * ldx + cc];
+            }
+            cfma(acc[0][c], t00, xa); cfma(acc[0][c], t01, xb);
+            cfma(acc[1][c], t10, xa); cfma(acc[1][c], t11, xb);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < R; ++c) red[warp][lane + 32 * q][c] = acc[q][c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < PH * R; e += NW * 32) {
+        const int li = e / R, c = e % R, row = P * PH + li, cc = s_col[c];
+        if (row >= n || cc < 0) continue;
+        C y = make_double2(0.0, 0.0);
+        for (int w = 0; w < NW; ++w) y = cadd(y, red[w][li][c]);
+        const C xr = X[(int64_t)row * ldx + cc];
+        cfms(y, s_z[c], xr);  // - z x_row
+        if (subtract) y = csub(B[(int64_t)row * ldb + cc], y);
+        Y[(int64_t)row * ldy + cc] = y;
+    }
+}
+
+constexpr int RMV = 4, NW_MV = 4;
+cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                          int ncols, const int *ncols_dev, const double2 *X, int64_t ldx, const double2 *B,
+                          int64_t ldb, double2 *Y, int64_t ldy, int subtract, cudaStream_t s) {
+    if (ncols <= 0) return cudaSuccess;
+    dim3 grid(n_pad / PH, (ncols + RMV - 1) / RMV);
+    trmv_ms_kernel<RMV, NW_MV><<<grid, NW_MV * 32, 0, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx,
+                                                           B, ldb, Y, ldy, subtract);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ norms
+__global__ void sumsq_kernel(const double2 *__restrict__ a, int64_t cnt, double *out) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        s += a[i].x * a[i].x + a[i].y * a[i].y;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(out, s);
+    }
+}
+
+cudaError_t launch_sumsq(const double2 *a, int64_t cnt, double *out, cudaStream_t s) {
+    cudaMemsetAsync(out, 0, sizeof(double), s);
+    sumsq_kernel<<<296, 256, 0, s>>>(a, cnt, out);
+    return cudaGetLastError();
+}
+
+__global__ void extract_diag_kernel(const double2 *__restrict__ U, int n, int n_pad, double2 *__restrict__ d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int P = i / PH, li = i % PH;
+    d[i] = U[upper_panel_offset(P, n_pad) + (int64_t)(li >> 1) * (2 * PH) + 2 * li + (li & 1)];
+}
+
+cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, cudaStream_t s) {
+    extract_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(U, n, n_pad, d);
+    return cudaGetLastError();
+}
+
+}  // namespace pseudo

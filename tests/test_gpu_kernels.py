@@ -1,0 +1,74 @@
+"""Multi-shift triangular solve and FP64 triangular product against the
+step-level oracle, on sizes that span several 64-row panels, ragged tails
+and 1/2/3-row matrices, with column counts that leave partial CTA groups."""
+import numpy as np
+import pytest
+
+from oracle import steps
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n, ncols, seed):
+    rng = np.random.default_rng(seed)
+    T = np.triu(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    T[np.arange(n), np.arange(n)] += 1.5 * np.exp(2j * np.pi * rng.random(n))
+    z = 0.5 * (rng.standard_normal(ncols) + 1j * rng.standard_normal(ncols))
+    B = rng.standard_normal((n, ncols)) + 1j * rng.standard_normal((n, ncols))
+    return T, z, B
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 100, 257])
+@pytest.mark.parametrize("ncols", [1, 3, 37])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_solve_fp64_and_mixed(n, ncols, adjoint):
+    import torch
+
+    import paper_2606_26785_b300 as p
+
+    T, z, B = _case(n, ncols, 1000 * n + ncols)
+    h = p.Pseudo(T)
+    ref = steps.shifted_solve(T, z, B, adjoint)
+    X = torch.from_numpy(B.copy()).cuda()
+    h.solve(X, z, adjoint=adjoint, precision=p.FP64)
+    got = X.cpu().numpy()
+    rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert rel.max() < 1e-12, rel.max()
+    X = torch.from_numpy(B.copy()).cuda()
+    h.solve(X, z, adjoint=adjoint, precision=p.MIXED)
+    got = X.cpu().numpy()
+    rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert rel.max() < 2e-4, rel.max()
+    h.close()
+
+
+@pytest.mark.parametrize("n", [1, 3, 65, 130])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_matvec_fp64(n, adjoint):
+    import torch
+
+    import paper_2606_26785_b300 as p
+
+    T, z, B = _case(n, 5, 7 + n)
+    X = np.random.default_rng(n).standard_normal((n, 5)) + 0j
+    h = p.Pseudo(T)
+    Xt = torch.from_numpy(X).cuda()
+    Y = h.matvec(Xt, z=z, adjoint=adjoint).cpu().numpy()
+    ref = steps.shifted_matvec(T, z, X, adjoint)
+    assert np.max(np.abs(Y - ref)) <= 1e-13 * np.max(np.abs(ref))
+    Bt = torch.from_numpy(B).cuda()
+    R = h.matvec(Xt, z=z, B=Bt, adjoint=adjoint).cpu().numpy()
+    assert np.max(np.abs(R - (B - ref))) <= 1e-13 * np.max(np.abs(B - ref))
+    h.close()
+
+
+def test_norms():
+    import paper_2606_26785_b300 as p
+
+    T, _, _ = _case(150, 1, 5)
+    h = p.Pseudo(T)
+    info = h.info()
+    assert abs(info["norm_fro"] - np.linalg.norm(T)) <= 1e-12 * np.linalg.norm(T)
+    s2 = np.linalg.norm(T, 2)
+    assert 0.9 * s2 <= info["norm2_est"] <= s2 * (1 + 1e-12)
+    h.close()
