@@ -22,7 +22,6 @@ import json
 import os
 import subprocess
 import sys
-import threading
 import time
 from pathlib import Path
 
@@ -111,6 +110,56 @@ def check_accuracy(sigma, W):
     return rep
 
 
+def _nominal_fp32_tflops(peaks):
+    """FP32 FMA pipe: 148 SMs x 128 lanes x 2 flops x max SM clock."""
+    return 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+
+
+FP64_MEASURED_TFLOPS = 1.13  # DFMA probe on this pool's B300 (see DESIGN.md section 0)
+
+
+def roofline(kst, peaks):
+    """Dominant kernel class of a profiled step and its achieved rate."""
+    name, k = max(kst.items(), key=lambda kv: kv[1]["ms"])
+    if k["launches"] == 0 or k["ms"] <= 0:
+        return None
+    per_launch_ms = k["ms"] / k["launches"]
+    flops = k["flops"] / k["launches"]
+    fp32 = _nominal_fp32_tflops(peaks)
+    if name in ("trsv32",):
+        peak, unit, bound = fp32, "TFLOP/s", "alu"
+    elif name == "trmv_ds":
+        # double-single: 12 FP32 operations per real multiply-add (2 algorithmic flops)
+        peak, unit, bound = fp32 / 6.0, "TFLOP/s", "alu"
+    elif name == "lanczos":
+        achieved = k["bytes"] / k["launches"] / (per_launch_ms / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "launches": k["launches"],
+                "avg_launch_ms": per_launch_ms, "peak_source": "measured"}
+    else:
+        peak, unit, bound = FP64_MEASURED_TFLOPS, "TFLOP/s", "alu"
+    achieved = flops / (per_launch_ms / 1e3) / 1e12
+    return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "launches": k["launches"], "avg_launch_ms": per_launch_ms,
+            "algorithmic_flops_per_launch": flops, "share_of_step": None,
+            "peak_source": "derived from 148 SMs x 128 FP32 lanes x max clock" if name in ("trsv32", "trmv_ds")
+            else "measured FP64 DFMA probe"}
+
+
+def cpu_baseline(W, budget_points=1):
+    import oracle
+
+    threads = os.cpu_count() or 1
+    rng = np.random.Generator(np.random.PCG64(11))
+    idx = rng.choice(W.z.size, size=budget_points, replace=False)
+    t0 = time.time()
+    oracle.sigma_min_grid(W.C, W.z[idx], threads=threads)
+    dt = time.time() - t0
+    return {"value": budget_points / dt, "unit": "points/s", "cores": threads, "kind": "oracle",
+            "sample": f"{budget_points} grid point(s) of the same workload, one-sided Jacobi SVD of the n=2000 "
+                      f"C - zI using all {threads} host threads inside the point; {dt:.1f} s"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -119,7 +168,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="recycle", choices=["recycle", "invlanc"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparison paths and the CPU baseline")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -140,16 +189,17 @@ def main():
     W, t_schur = make_workload()
     h = p.Pseudo(W.T)
     prec = p.MIXED if args.precision == "mixed" else p.FP64
+    rtol = 1e-8 if prec == p.MIXED else 1e-10
     if args.mode == "recycle":
         opts = p.default_opts(mode=p.RECYCLE, precision=prec, r=4, p_max=4, grid_nx=W.nx, grid_ny=W.ny,
-                              batch_b=20, rtol=1e-8 if prec == p.MIXED else 1e-10)
+                              batch_b=20, rtol=rtol)
     else:
-        opts = p.default_opts(mode=p.INVLANC, precision=prec, rtol=1e-8 if prec == p.MIXED else 1e-10)
+        opts = p.default_opts(mode=p.INVLANC, precision=prec, rtol=rtol)
     z = torch.from_numpy(W.z).cuda()
     need = h.workspace_bytes(W.z.size, opts)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    eps = W.meta.get("eps", (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10))
+    eps = (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10)
 
     def step():
         return h.grid(z, eps, opts=opts, workspace=ws)
@@ -159,7 +209,9 @@ def main():
     torch.cuda.synchronize()
     h.reset_stats()
     times = []
-    clocks = Clocks(str(ROOT / "gpurun_out" / "bench_clocks.csv") if (ROOT / "gpurun_out").exists() else "/tmp/bench_clocks.csv")
+    out_dir = ROOT / "gpurun_out"
+    clocks = Clocks(str(out_dir / "bench_clocks.csv") if out_dir.exists() else "/tmp/bench_clocks.csv")
+    lc0 = p._abi.load().pseudo_launch_count()
     with clocks:
         for _ in range(args.steps):
             flush.zero_()
@@ -175,6 +227,7 @@ def main():
             if dist:
                 dist.barrier()
             times.append(e0.elapsed_time(e1))
+    launches = p._abi.load().pseudo_launch_count() - lc0
     ms = float(np.mean(times))
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -185,6 +238,73 @@ def main():
     acc = check_accuracy(sigma, W)
     npts = W.z.size
     value = npts * world / (ms / 1e3)
+    peaks = _peaks()
+
+    # one profiled step: per-kernel CUDA-event times on the launching stream
+    h.reset_stats()
+    opts.profile = 1
+    step()
+    torch.cuda.synchronize()
+    opts.profile = 0
+    kst = h.kernel_stats()
+    prof_ms = h.stats()["ms_total"]
+    rf = roofline(kst, peaks)
+    if rf is not None:
+        rf["share_of_step"] = kst[rf["kernel"]]["ms"] / max(prof_ms, 1e-9)
+
+    # end to end through the host-buffer C-ABI call (z in, results out, copies inside)
+    zpin = torch.from_numpy(W.z.copy()).pin_memory().numpy()
+    outs = {"sigma": torch.empty(npts, dtype=torch.float64).pin_memory().numpy(),
+            "res": torch.empty(npts, dtype=torch.float64).pin_memory().numpy(),
+            "flags": torch.empty(npts, dtype=torch.int32).pin_memory().numpy(),
+            "member": torch.empty(npts, dtype=torch.int32).pin_memory().numpy().view(np.uint32)}
+    hopts = p.Opts.from_buffer_copy(opts)
+    hopts.io_host = 1
+    del ws
+    e2e_ws = torch.empty(h.workspace_bytes(npts, hopts), dtype=torch.uint8, device="cuda")
+    h.grid_host(zpin, eps, opts=hopts, workspace=e2e_ws, out=outs)
+    e2e_t = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.grid_host(zpin, eps, opts=hopts, workspace=e2e_ws, out=outs)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e = {"value": npts / float(np.mean(e2e_t)), "unit": "points/s", "h2d_bytes_per_step": int(npts * 16),
+           "d2h_bytes_per_step": int(npts * (8 + 8 + 4 + 4))}
+
+    extras = {}
+    cpu = None
+    if not args.no_extras and rank == 0:
+        # plain FP64 inverse Lanczos, batched and one point per launch, on bounded samples of the grid
+        sub = torch.from_numpy(W.z[::20].copy()).cuda()
+        for name, kw, zz in (
+            ("invlanc_fp64_batched", dict(mode=p.INVLANC, precision=p.FP64, rtol=1e-10), sub),
+            ("invlanc_mixed_batched", dict(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8), sub),
+            ("invlanc_fp64_per_point", dict(mode=p.INVLANC, precision=p.FP64, rtol=1e-10, shift_batch=1), sub[:8]),
+        ):
+            o2 = p.default_opts(**kw)
+            h.grid(zz[:4], eps, opts=o2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.grid(zz, eps, opts=o2)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            extras[name] = {"points": int(zz.numel()), "points_per_s": zz.numel() / dt}
+        o3 = p.default_opts(mode=p.RECYCLE, precision=p.FP64, r=4, p_max=4, grid_nx=W.nx, grid_ny=W.ny, batch_b=20,
+                            rtol=1e-10)
+        ws3 = torch.empty(h.workspace_bytes(npts, o3), dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = h.grid(z, eps, opts=o3, workspace=ws3)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        extras["recycle_fp64"] = {"points": npts, "points_per_s": npts / dt,
+                                  "accuracy_rtol_1e-10": check_accuracy_rtol(o["sigma"].cpu().numpy(), W, 1e-10)}
+        del ws3
+        cpu = cpu_baseline(W)
+
     result = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -192,12 +312,27 @@ def main():
         "config": {"workload": WORKLOAD, "mode": args.mode, "precision": args.precision, "k": 16, "r": 4,
                    "batch_b": 20, "points": npts, "l2": "flushed (256 MB write) between timed steps",
                    "schur_seconds_host_untimed": t_schur},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": rf,
+        "cpu_baseline": cpu,
+        "clocks": clocks.summary(),
         "accuracy": acc,
-        "counters": {k: v / max(1, args.steps) if isinstance(v, (int, float)) else v for k, v in st.items()},
-        "gpu_launches": None,
+        "counters_per_step": {k: (v / max(1, args.steps)) for k, v in st.items()},
+        "kernels_profiled_step": kst,
+        "comparisons": extras,
     }
     if rank == 0:
         print(json.dumps(result))
+
+
+def check_accuracy_rtol(sigma, W, rtol):
+    from tests.parity import check_sigma
+
+    g = json.loads(GOLDEN.read_text())
+    idx = np.array(g["index"])
+    return check_sigma(np.asarray(sigma)[idx], np.array(g["sigma_ref"]), n=W.n, fro=g["fro_norm"],
+                       schur_err=W.schur_err, oracle_off=np.array(g["oracle_off"]), rtol=rtol)
 
 
 def run_reference(args, rank, world):

@@ -92,6 +92,8 @@ typedef struct {
     int max_ir;          /* iterative-refinement steps cap per solve (mixed precision) */
     int io_host;        /* 1: z/sigma/res/flags/member pointers of pseudo_grid are host memory */
     uint64_t seed;      /* seed of the random start vectors */
+    int profile;        /* 1: time every hot-kernel launch with CUDA events (pseudo_kernel_stats) */
+    int reserved;
 } pseudo_opts;
 
 typedef struct {
@@ -107,6 +109,26 @@ typedef struct {
     int64_t lobpcg_iters;
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
 } pseudo_stats_t;
+
+/* Per-kernel-class accounting (filled when pseudo_opts.profile = 1): launches,
+ * device time from CUDA events recorded on the launching stream around each
+ * launch, and the algorithmic work of those launches (flops: real floating-point
+ * operations of the textbook algorithm, 8 per complex multiply-add; bytes: the
+ * operands each launch must read and write at least once). */
+enum {
+    PSEUDO_K_TRSV32 = 0,  /* multi-shift triangular solve, FP32 arithmetic */
+    PSEUDO_K_TRSV64,      /* multi-shift triangular solve, FP64 */
+    PSEUDO_K_TRMV64,      /* triangular product / residual, FP64 */
+    PSEUDO_K_TRMV_DS,     /* triangular product / residual, double-single on FP32 units */
+    PSEUDO_K_RECYSING,    /* recycled Rayleigh--Ritz-SVD + residual, one CTA per point */
+    PSEUDO_K_LANCZOS,     /* Lanczos reorthogonalisation */
+    PSEUDO_K_COUNT
+};
+typedef struct {
+    int64_t launches;
+    double ms, flops, bytes;
+} pseudo_kstat;
+int pseudo_kernel_stats(pseudo_handle h, int kclass, pseudo_kstat *out);
 
 /* Fill *o with defaults. Returns PSEUDO_OK or PSEUDO_ERR_ARG (o == NULL). */
 int pseudo_opts_default(pseudo_opts *o);
@@ -157,6 +179,10 @@ void pseudo_destroy(pseudo_handle h);
 /* Thread-local message describing the last non-OK return ("" if none). */
 const char *pseudo_last_error(void);
 
+/* Number of CUDA kernel launches the library has made in this process (all
+ * handles, all threads); differences around a call count its launches. */
+int64_t pseudo_launch_count(void);
+
 /* ---- kernel-level entry points (used by the tests; same rules as above) ----
  *
  * pseudo_solve: X[:, c] <- (T - z_c I)^{-1} X[:, c] (adjoint = 0) or
@@ -167,14 +193,18 @@ const char *pseudo_last_error(void);
  *   z   : device, ncols complex shifts, one per column.
  *   precision : PSEUDO_FP64 (all FP64) or PSEUDO_MIXED (FP32 arithmetic).
  *   workspace : device, >= pseudo_solve_workspace_bytes bytes.
- * pseudo_matvec: Y[:, c] <- B[:, c] - beta * (T - z_c I)^{op} X[:, c] in FP64, with
- *   beta in {+1, -1} given by subtract (1: B - AX, 0: AX, B ignored and may be NULL).
- *   X, Y, B device row-major n x ncols complex; Y must not alias X. */
+ * pseudo_matvec: Y[:, c] <- B[:, c] - (T - z_c I)^{op} X[:, c] (subtract = 1) or
+ *   Y[:, c] <- (T - z_c I)^{op} X[:, c] (subtract = 0, B ignored and may be NULL); the
+ *   refinement residual of a shifted solve and the products T V, T^H V of Alg. 2.
+ *   precision PSEUDO_FP64: IEEE double arithmetic; PSEUDO_MIXED: double-single
+ *   arithmetic on the FP32 units (T split into two FP32 planes, exact products and
+ *   two-sums; relative error about 2^-46).
+ *   X, Y, B device row-major n x ncols complex; Y must not alias X. z may be NULL (z = 0). */
 int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
 int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
                  int precision, void *workspace, size_t workspace_bytes, void *stream);
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
-                  const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, void *stream);
+                  const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision, void *stream);
 
 #ifdef __cplusplus
 }

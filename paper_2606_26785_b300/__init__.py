@@ -83,6 +83,14 @@ class Pseudo:
         check(self._lib.pseudo_stats(self._h, ctypes.byref(s)))
         return s.as_dict()
 
+    def kernel_stats(self) -> dict:
+        out = {}
+        for i, name in enumerate(_abi.KCLASSES):
+            k = _abi.KStat()
+            check(self._lib.pseudo_kernel_stats(self._h, i, ctypes.byref(k)))
+            out[name] = {"launches": k.launches, "ms": k.ms, "flops": k.flops, "bytes": k.bytes}
+        return out
+
     def reset_stats(self):
         check(self._lib.pseudo_stats_reset(self._h))
 
@@ -153,12 +161,13 @@ class Pseudo:
                                      b.value, _stream_ptr(stream)))
         return X
 
-    def matvec(self, X, z=None, B=None, adjoint: bool = False, stream=None):
-        """Y = (T - zI)^{op} X, or B - (T - zI)^{op} X when B is given (FP64)."""
+    def matvec(self, X, z=None, B=None, adjoint: bool = False, precision: int = FP64, stream=None):
+        """Y = (T - zI)^{op} X, or B - (T - zI)^{op} X when B is given; FP64 or
+        double-single (precision=MIXED) arithmetic."""
         torch = _torch()
         ncols = X.shape[1]
         Y = torch.empty_like(X)
         zt = None if z is None else torch.as_tensor(z).to(device="cuda", dtype=torch.complex128).contiguous()
         check(self._lib.pseudo_matvec(self._h, _ptr(X), _ptr(B), _ptr(Y), _ptr(zt), ncols, int(adjoint),
-                                      int(B is not None), _stream_ptr(stream)))
+                                      int(B is not None), int(precision), _stream_ptr(stream)))
         return Y

@@ -16,7 +16,7 @@ PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4
 EXPORTED = (
     "pseudo_opts_default", "pseudo_create", "pseudo_workspace_bytes", "pseudo_grid", "pseudo_stats",
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
-    "pseudo_solve", "pseudo_matvec",
+    "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count",
 )
 
 
@@ -27,8 +27,16 @@ class Opts(ctypes.Structure):
         ("shift_batch", ctypes.c_int), ("eps_shift_rel", ctypes.c_double), ("tau", ctypes.c_double),
         ("omega", ctypes.c_double), ("eta", ctypes.c_double), ("rtol", ctypes.c_double),
         ("maxiter_lanczos", ctypes.c_int), ("maxiter_lobpcg", ctypes.c_int), ("max_ir", ctypes.c_int),
-        ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64),
+        ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
+
+
+class KStat(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos")
 
 
 class Stats(ctypes.Structure):
@@ -74,10 +82,13 @@ def load(build_if_missing: bool = True):
     lib.pseudo_last_error.restype = ctypes.c_char_p
     lib.pseudo_solve_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_solve.argtypes = [vp, vp, vp, i64, ci, ci, vp, ctypes.c_size_t, vp]
-    lib.pseudo_matvec.argtypes = [vp, vp, vp, vp, vp, i64, ci, ci, vp]
+    lib.pseudo_launch_count.argtypes = []
+    lib.pseudo_launch_count.restype = ctypes.c_int64
+    lib.pseudo_kernel_stats.argtypes = [vp, ci, ctypes.POINTER(KStat)]
+    lib.pseudo_matvec.argtypes = [vp, vp, vp, vp, vp, i64, ci, ci, ci, vp]
     for name in EXPORTED:
         fn = getattr(lib, name)
-        if name not in ("pseudo_destroy", "pseudo_last_error"):
+        if name not in ("pseudo_destroy", "pseudo_last_error", "pseudo_launch_count"):
             fn.restype = ctypes.c_int
     _lib = lib
     return lib

@@ -145,33 +145,33 @@ __global__ void nonfinite_kernel(const double2 *__restrict__ a, int64_t cnt, int
 // ------------------------------------------------------------ launchers
 static inline unsigned cgroups(int S) { return (unsigned)((S + 31) / 32); }
 void launch_colnorm2(const double2 *X, int n, int S, const int *mask, double *out, cudaStream_t s) {
-    colnorm2_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask, out);
+    note_launch(); colnorm2_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask, out);
 }
 void launch_scale_to32(const double2 *R, int n, int S, const int *mask, const double *rn2, float2 *D, cudaStream_t s) {
-    scale_to32_kernel<<<cgroups(S), CW * 32, 0, s>>>(R, n, S, mask, rn2, D);
+    note_launch(); scale_to32_kernel<<<cgroups(S), CW * 32, 0, s>>>(R, n, S, mask, rn2, D);
 }
 void launch_acc_from32(double2 *X, int n, int S, const int *mask, const double *rn2, const float2 *D, cudaStream_t s) {
-    acc_from32_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask, rn2, D);
+    note_launch(); acc_from32_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask, rn2, D);
 }
 void launch_normalize(double2 *X, int n, int S, const int *mask, cudaStream_t s) {
-    normalize_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask);
+    note_launch(); normalize_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask);
 }
 void launch_rq_residual(const double2 *U, const double2 *Y, const double2 *NX, int n, int S, const int *mask,
                         double *s2, double *r, cudaStream_t s) {
-    rq_residual_kernel<<<cgroups(S), CW * 32, 0, s>>>(U, Y, NX, n, S, mask, s2, r);
+    note_launch(); rq_residual_kernel<<<cgroups(S), CW * 32, 0, s>>>(U, Y, NX, n, S, mask, s2, r);
 }
 void launch_finalize(int S, int64_t w0, const double2 *z, const double *theta, const double *s2, const double *rr,
                      const int *active, const int *extra_flags, int sig_src, double norm2, const double *eps, int neps,
                      double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int base_flags,
                      int *nbad, cudaStream_t s) {
-    finalize_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, w0, z, theta, s2, rr, active, extra_flags, sig_src, norm2, eps,
+    note_launch(); finalize_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, w0, z, theta, s2, rr, active, extra_flags, sig_src, norm2, eps,
                                                     neps, sigma_out, res_out, flags_out, member_out, base_flags, nbad);
 }
 void launch_fill_int(int *a, int n, int v, cudaStream_t s) {
-    if (n > 0) fill_int_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, n, v);
+    if (n > 0) { note_launch(); fill_int_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, n, v); }
 }
 void launch_nonfinite(const double2 *a, int64_t cnt, int *bad, cudaStream_t s) {
-    nonfinite_kernel<<<296, 256, 0, s>>>(a, cnt, bad);
+    note_launch(); nonfinite_kernel<<<296, 256, 0, s>>>(a, cnt, bad);
 }
 
 }  // namespace pseudo
@@ -186,9 +186,9 @@ __global__ void cvt32to64_kernel(const float2 *__restrict__ a, double2 *__restri
         b[i] = make_double2((double)a[i].x, (double)a[i].y);
 }
 void launch_convert_64_to_32(const double2 *a, float2 *b, int64_t cnt, cudaStream_t s) {
-    if (cnt > 0) cvt64to32_kernel<<<1184, 256, 0, s>>>(a, b, cnt);
+    if (cnt > 0) { note_launch(); cvt64to32_kernel<<<1184, 256, 0, s>>>(a, b, cnt); }
 }
 void launch_convert_32_to_64(const float2 *a, double2 *b, int64_t cnt, cudaStream_t s) {
-    if (cnt > 0) cvt32to64_kernel<<<1184, 256, 0, s>>>(a, b, cnt);
+    if (cnt > 0) { note_launch(); cvt32to64_kernel<<<1184, 256, 0, s>>>(a, b, cnt); }
 }
 }  // namespace pseudo

@@ -7,6 +7,9 @@
 
 namespace pseudo {
 
+// Counts every kernel launch the library makes (process-wide).
+void note_launch();
+
 // ---------------------------------------------------------------- complex
 template <typename real> struct cx;
 template <> struct cx<double> { using t = double2; };

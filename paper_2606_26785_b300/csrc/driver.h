@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "pseudo.h"
+#include "internal.h"
 
 namespace pseudo {
 constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
@@ -35,21 +36,83 @@ struct GridIO {
 };
 }  // namespace pseudo
 
+#include <vector>
+
 struct pseudo_ctx {
     int dev = 0;
+    // per-kernel-class profiling (pseudo_opts.profile)
+    struct KRec {
+        int cls, ea, eb;
+        double flops, bytes;
+    };
+    bool prof = false;
+    std::vector<cudaEvent_t> evs;
+    int evn = 0;
+    std::vector<KRec> recs;
+    pseudo_kstat kst[PSEUDO_K_COUNT] = {};
     int n = 0, n_pad = 0;
     double2 *U64 = nullptr, *L64 = nullptr;  // packed panels of T and T^H, FP64
-    float2 *U32 = nullptr, *L32 = nullptr;   // the same in FP32
+    float2 *U32 = nullptr, *L32 = nullptr;   // the same in FP32 (the high parts)
+    float2 *U32lo = nullptr, *L32lo = nullptr;  // fl32(T - fl32(T)): low parts for double-single products
     double2 *diag = nullptr;                 // T_ii (the eigenvalues of C)
     double norm_fro = 0.0, norm2 = 0.0;      // ||T||_F and a 2-norm estimate
     pseudo_stats_t stats;
 };
 
 namespace pseudo {
+inline int kp_begin(pseudo_ctx *h, cudaStream_t s) {
+    if (!h->prof) return -1;
+    if (h->evn >= (int)h->evs.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->evs.push_back(e);
+    }
+    cudaEventRecord(h->evs[h->evn], s);
+    return h->evn++;
+}
+inline void kp_end(pseudo_ctx *h, int ea, int cls, double flops, double bytes, cudaStream_t s) {
+    if (ea < 0) return;
+    const int eb = kp_begin(h, s);
+    h->recs.push_back({cls, ea, eb, flops, bytes});
+}
+// After the stream has been synchronised: fold the event pairs into kst.
+inline void kp_resolve(pseudo_ctx *h) {
+    for (const auto &r : h->recs) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->evs[r.ea], h->evs[r.eb]);
+        h->kst[r.cls].launches += 1;
+        h->kst[r.cls].ms += ms;
+        h->kst[r.cls].flops += r.flops;
+        h->kst[r.cls].bytes += r.bytes;
+    }
+    h->recs.clear();
+    h->evn = 0;
+}
+// algorithmic work of one multi-shift solve / product launch on ncols columns
+inline double tri_flops(int n, int ncols) { return 4.0 * (double)n * n * ncols; }
+inline double tri_bytes(int n, int ncols, double tri_esz, double vec_esz, int nvec) {
+    return 0.5 * (double)n * n * tri_esz + (double)nvec * n * ncols * vec_esz;
+}
+
 void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *plan);
 int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
 void recycle_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *plan);
 int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
 void launch_convert_64_to_32(const double2 *a, float2 *b, int64_t cnt, cudaStream_t s);
 void launch_convert_32_to_64(const float2 *a, double2 *b, int64_t cnt, cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+// (T - zI)^{op} products for the refinement residuals and the recycled
+// subspace: IEEE FP64 in FP64 mode, double-single on the FP32 units in mixed
+// mode.
+inline cudaError_t trmv_hp(pseudo_ctx *h, bool ds, int lower, const int *cols, const double2 *zc, int ncols,
+                           const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
+                           int subtract, cudaStream_t s) {
+    if (ds)
+        return launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, cols, zc,
+                              ncols, X, ldx, B, ldb, Y, ldy, subtract, s);
+    return launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, cols, zc, ncols, nullptr, X, ldx, B, ldb, Y,
+                         ldy, subtract, s);
+}
 }  // namespace pseudo

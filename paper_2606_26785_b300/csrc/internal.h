@@ -19,6 +19,10 @@ cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const i
 cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
                           int ncols, const int *ncols_dev, const double2 *X, int64_t ldx, const double2 *B,
                           int64_t ldb, double2 *Y, int64_t ldy, int subtract, cudaStream_t s);
+cudaError_t launch_trmv_ds(const float2 *Ph, const float2 *Pl, int n, int n_pad, int lower, const int *cols,
+                           const double2 *zc, int ncols, const double2 *X, int64_t ldx, const double2 *B, int64_t ldb,
+                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s);
+void launch_pack_lo(const double2 *P64, const float2 *P32, float2 *Plo, int64_t cnt, cudaStream_t s);
 cudaError_t launch_sumsq(const double2 *a, int64_t cnt, double *out, cudaStream_t s);
 cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, cudaStream_t s);
 

@@ -99,12 +99,15 @@ static cudaError_t ir_solve(pseudo_ctx *h, const LancLayout &L, int lower, const
     for (int it = 0; it < max_ir; ++it) {
         launch_colnorm2(L.R64, n, Sw, nullptr, L.rn2, s);
         launch_scale_to32(L.R64, n, Sw, nullptr, L.rn2, D32, s);
+        int k0 = kp_begin(h, s);
         cudaError_t e = launch_trsv32(lower ? h->L32 : h->U32, n, h->n_pad, lower, nullptr, zc, Sw, nullptr, D32, Sw,
                                       (float2 *)L.xs, s);
+        kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, Sw), tri_bytes(n, Sw, 8, 8, 2), s);
         if (e != cudaSuccess) return e;
         launch_acc_from32(X, n, Sw, nullptr, L.rn2, D32, s);
-        e = launch_trmv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, nullptr, zc, Sw, nullptr, X, Sw, B, Sw, L.R64,
-                          Sw, 1, s);
+        k0 = kp_begin(h, s);
+        e = trmv_hp(h, true, lower, nullptr, zc, Sw, X, Sw, B, Sw, L.R64, Sw, 1, s);
+        kp_end(h, k0, PSEUDO_K_TRMV_DS, tri_flops(n, Sw), tri_bytes(n, Sw, 16, 16, 3), s);
         if (e != cudaSuccess) return e;
         h->stats.sv_R += Sw;
         h->stats.mv_M_fp64_refine += Sw;
@@ -157,17 +160,29 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             if (L.fp32) {
                 float2 *Q = (float2 *)L.Q, *W = (float2 *)L.W;
                 launch_copy_cols<float>(Q + (int64_t)j * qs, W, n, Sw, L.active, s);
+                int k0 = kp_begin(h, s);
                 e = launch_trsv32(h->L32, n, h->n_pad, 1, L.cols, zc, ncnt, L.cnt, W, Sw, (float2 *)L.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
+                k0 = kp_begin(h, s);
                 if (e == cudaSuccess)
                     e = launch_trsv32(h->U32, n, h->n_pad, 0, L.cols, zc, ncnt, L.cnt, W, Sw, (float2 *)L.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
+                k0 = kp_begin(h, s);
                 launch_lanczos_orth<float>(Q, qs, W, n, Sw, j, L.mmax, L.active, L.alpha, L.beta, s);
+                kp_end(h, k0, PSEUDO_K_LANCZOS, 32.0 * (j + 1) * n * ncnt, 4.0 * (j + 2) * n * ncnt * 8, s);
             } else {
                 double2 *Q = (double2 *)L.Q, *W = (double2 *)L.W;
                 launch_copy_cols<double>(Q + (int64_t)j * qs, W, n, Sw, L.active, s);
+                int k0 = kp_begin(h, s);
                 e = launch_trsv64(h->L64, n, h->n_pad, 1, L.cols, zc, ncnt, L.cnt, W, Sw, (double2 *)L.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
+                k0 = kp_begin(h, s);
                 if (e == cudaSuccess)
                     e = launch_trsv64(h->U64, n, h->n_pad, 0, L.cols, zc, ncnt, L.cnt, W, Sw, (double2 *)L.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
+                k0 = kp_begin(h, s);
                 launch_lanczos_orth<double>(Q, qs, W, n, Sw, j, L.mmax, L.active, L.alpha, L.beta, s);
+                kp_end(h, k0, PSEUDO_K_LANCZOS, 32.0 * (j + 1) * n * ncnt, 4.0 * (j + 2) * n * ncnt * 16, s);
             }
             if (e != cudaSuccess) return cuda_err(e, "lanczos solve");
             h->stats.sv_R += 2 * (int64_t)ncnt;
@@ -189,8 +204,13 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             cudaMemcpyAsync(L.U, L.X64, (size_t)n * Sw * sizeof(double2), cudaMemcpyDeviceToDevice, s);
         }
         // Rayleigh quotient and residual of the returned vector, in FP64
-        launch_trmv64(h->U64, n, h->n_pad, 0, nullptr, zc, Sw, nullptr, L.U, Sw, nullptr, Sw, L.Y, Sw, 0, s);
-        launch_trmv64(h->L64, n, h->n_pad, 1, nullptr, zc, Sw, nullptr, L.Y, Sw, nullptr, Sw, L.NX, Sw, 0, s);
+        {
+            const int kc = L.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
+            int k0 = kp_begin(h, s);
+            trmv_hp(h, L.fp32, 0, nullptr, zc, Sw, L.U, Sw, nullptr, Sw, L.Y, Sw, 0, s);
+            trmv_hp(h, L.fp32, 1, nullptr, zc, Sw, L.Y, Sw, nullptr, Sw, L.NX, Sw, 0, s);
+            kp_end(h, k0, kc, 2 * tri_flops(n, Sw), 2 * tri_bytes(n, Sw, 16, 16, 2), s);
+        }
         h->stats.mv_M_fp64_refine += 2 * (int64_t)Sw;
         launch_rq_residual(L.U, L.Y, L.NX, n, Sw, nullptr, L.s2, L.rr, s);
         launch_finalize(Sw, w0, zc, L.theta, L.s2, L.rr, L.active, nullptr, L.fp32 ? 1 : 0, h->norm2, L.eps, io.neps,

@@ -342,35 +342,35 @@ ritz_vector_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, i
 
 // ------------------------------------------------------------ launchers
 void launch_start_vector(double2 *v, int n, uint64_t seed, cudaStream_t s) {
-    start_vector_kernel<<<1, 1024, 0, s>>>(v, n, seed);
+    note_launch(); start_vector_kernel<<<1, 1024, 0, s>>>(v, n, seed);
 }
 template <typename real>
 void launch_bcast_start(const double2 *v, int n, int S, cx_t<real> *Q0, cudaStream_t s) {
     int64_t tot = (int64_t)n * S;
-    bcast_start_kernel<real><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(v, n, S, Q0);
+    note_launch(); bcast_start_kernel<real><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(v, n, S, Q0);
 }
 template <typename real>
 void launch_copy_cols(const cx_t<real> *src, cx_t<real> *dst, int n, int S, const int *active, cudaStream_t s) {
-    copy_cols_kernel<real><<<(S + 31) / 32, 256, 0, s>>>(src, dst, n, S, active);
+    note_launch(); copy_cols_kernel<real><<<(S + 31) / 32, 256, 0, s>>>(src, dst, n, S, active);
 }
 template <typename real>
 void launch_lanczos_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, int j, int mmax, const int *active,
                          double *alpha, double *beta, cudaStream_t s) {
-    lanczos_orth_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, j, mmax, active, alpha, beta);
+    note_launch(); lanczos_orth_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, j, mmax, active, alpha, beta);
 }
 void launch_lanczos_tridiag(int S, int j, int mmax, const double *alpha, const double *beta, int *active,
                             double *theta, double *svec, int *nsteps, double tol_q, double tol_floor, int final_step,
                             cudaStream_t s) {
-    lanczos_tridiag_kernel<<<(S + 63) / 64, 64, 0, s>>>(S, j, mmax, alpha, beta, active, theta, svec, nsteps, tol_q,
+    note_launch(); lanczos_tridiag_kernel<<<(S + 63) / 64, 64, 0, s>>>(S, j, mmax, alpha, beta, active, theta, svec, nsteps, tol_q,
                                                         tol_floor, final_step);
 }
 void launch_compact_active(const int *active, int S, int *cols, int *cnt, cudaStream_t s) {
-    compact_active_kernel<<<1, 1024, 0, s>>>(active, S, cols, cnt);
+    note_launch(); compact_active_kernel<<<1, 1024, 0, s>>>(active, S, cols, cnt);
 }
 template <typename real>
 void launch_ritz_vector(const cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, const int *nsteps,
                         double2 *U, const int *mask, cudaStream_t s) {
-    ritz_vector_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, n, S, mmax, svec, nsteps, U, mask);
+    note_launch(); ritz_vector_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, n, S, mmax, svec, nsteps, U, mask);
 }
 
 template void launch_bcast_start<float>(const double2 *, int, int, float2 *, cudaStream_t);

@@ -223,34 +223,34 @@ __global__ void copy_listed_kernel(const S *__restrict__ src, D *__restrict__ ds
 // ------------------------------------------------------------ launchers
 cudaError_t launch_chol_rinv(const double2 *Gram, int m, int nitems, const int *items, double2 *Rinv, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    chol_rinv_kernel<<<nitems, LB_THREADS, 0, s>>>(Gram, m, items, Rinv);
+    note_launch(); chol_rinv_kernel<<<nitems, LB_THREADS, 0, s>>>(Gram, m, items, Rinv);
     return cudaGetLastError();
 }
 cudaError_t launch_lob_rr(const double2 *Gram, int m, int r, int with_p, int nitems, const int *items, double *xi,
                           double2 *GX, double2 *GP, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    lob_rr_kernel<<<nitems, LB_THREADS, 0, s>>>(Gram, m, r, with_p, items, xi, GX, GP);
+    note_launch(); lob_rr_kernel<<<nitems, LB_THREADS, 0, s>>>(Gram, m, r, with_p, items, xi, GX, GP);
     return cudaGetLastError();
 }
 cudaError_t launch_lob_resid(double2 *S, const double2 *Y, int n, int64_t ld, int r, int nitems, const int *items,
                              const double *xi, double eta, double rtol, int *conv, double *wnorm, cudaStream_t s) {
     if (nitems <= 0) return cudaSuccess;
-    lob_resid_kernel<<<nitems, LB_THREADS, 0, s>>>(S, Y, n, ld, r, items, xi, eta, rtol, conv, wnorm);
+    note_launch(); lob_resid_kernel<<<nitems, LB_THREADS, 0, s>>>(S, Y, n, ld, r, items, xi, eta, rtol, conv, wnorm);
     return cudaGetLastError();
 }
 void launch_expand_shift(const double2 *z, int nitems, int r, double2 *zcol, cudaStream_t s) {
     const int t = nitems * 3 * r;
-    if (t > 0) expand_shift_kernel<<<(t + 255) / 256, 256, 0, s>>>(z, nitems, r, zcol);
+    if (t > 0) { note_launch(); expand_shift_kernel<<<(t + 255) / 256, 256, 0, s>>>(z, nitems, r, zcol); }
 }
 void launch_make_cols(const int *items, int nact, int r, int off, int *cols, cudaStream_t s) {
     const int t = nact * r;
-    if (t > 0) make_cols_kernel<<<(t + 255) / 256, 256, 0, s>>>(items, nact, r, off, cols);
+    if (t > 0) { note_launch(); make_cols_kernel<<<(t + 255) / 256, 256, 0, s>>>(items, nact, r, off, cols); }
 }
 template <typename S, typename D>
 void launch_copy_listed(const S *src, D *dst, int n, int64_t ld, const int *cols, int ncols, int soff, int doff, int r3,
                         const double *scale, int sstride, int invert, cudaStream_t s) {
     if (ncols > 0)
-        copy_listed_kernel<S, D><<<(ncols + 31) / 32, 256, 0, s>>>(src, dst, n, ld, cols, ncols, soff, doff, r3, scale,
+        note_launch(); copy_listed_kernel<S, D><<<(ncols + 31) / 32, 256, 0, s>>>(src, dst, n, ld, cols, ncols, soff, doff, r3, scale,
                                                                    sstride, invert);
 }
 template void launch_copy_listed<double2, double2>(const double2 *, double2 *, int, int64_t, const int *, int, int, int,

@@ -13,7 +13,12 @@
 #include "pseudo.h"
 #include "driver.h"
 
+#include <atomic>
+
 namespace pseudo {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
 
@@ -47,6 +52,8 @@ using namespace pseudo;
 extern "C" {
 
 const char *pseudo_last_error(void) { return g_err.c_str(); }
+
+int64_t pseudo_launch_count(void) { return (int64_t)g_launches.load(); }
 
 int pseudo_opts_default(pseudo_opts *o) {
     if (!o) return set_err(PSEUDO_ERR_ARG, "opts is NULL");
@@ -98,6 +105,8 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaMalloc(&h->L64, psz * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L64"));
     if ((e = cudaMalloc(&h->U32, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc U32"));
     if ((e = cudaMalloc(&h->L32, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L32"));
+    if ((e = cudaMalloc(&h->U32lo, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc U32lo"));
+    if ((e = cudaMalloc(&h->L32lo, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L32lo"));
     if ((e = cudaMalloc(&h->diag, n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc diag"));
     if ((e = cudaMalloc(&bad, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if ((e = cudaMalloc(&dsum, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
@@ -109,6 +118,8 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
         Td = (double2 *)T;
     }
     launch_pack_panels(Td, ldT, (int)n, h->n_pad, h->U64, h->L64, h->U32, h->L32, s);
+    launch_pack_lo(h->U64, h->U32, h->U32lo, psz, s);
+    launch_pack_lo(h->L64, h->L32, h->L32lo, psz, s);
     cudaMemsetAsync(bad, 0, sizeof(int), s);
     launch_nonfinite(h->U64, psz, bad, s);
     launch_extract_diag(h->U64, (int)n, h->n_pad, h->diag, s);
@@ -159,7 +170,10 @@ void pseudo_destroy(pseudo_handle h) {
     cudaFree(h->L64);
     cudaFree(h->U32);
     cudaFree(h->L32);
+    cudaFree(h->U32lo);
+    cudaFree(h->L32lo);
     cudaFree(h->diag);
+    for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     delete h;
 }
 
@@ -180,6 +194,13 @@ int pseudo_stats(pseudo_handle h, pseudo_stats_t *out) {
 int pseudo_stats_reset(pseudo_handle h) {
     if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
     memset(&h->stats, 0, sizeof h->stats);
+    memset(h->kst, 0, sizeof h->kst);
+    return PSEUDO_OK;
+}
+
+int pseudo_kernel_stats(pseudo_handle h, int kclass, pseudo_kstat *out) {
+    if (!h || !out || kclass < 0 || kclass >= PSEUDO_K_COUNT) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    *out = h->kst[kclass];
     return PSEUDO_OK;
 }
 
@@ -224,15 +245,23 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
 }
 
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y, const pseudo_c64 *z,
-                  int64_t ncols, int adjoint, int subtract, void *stream) {
+                  int64_t ncols, int adjoint, int subtract, int precision, void *stream) {
     clear_err();
     if (!h || !X || !Y || ncols < 0 || (subtract && !B)) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED) return set_err(PSEUDO_ERR_ARG, "bad precision");
+    if (ncols > (1 << 18)) return set_err(PSEUDO_ERR_ARG, "ncols too large");
     if ((const void *)X == (const void *)Y) return set_err(PSEUDO_ERR_ARG, "Y must not alias X");
     if (ncols == 0) return PSEUDO_OK;
     const int lower = adjoint ? 1 : 0;
-    cudaError_t e = launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z,
-                                  (int)ncols, nullptr, (const double2 *)X, ncols, (const double2 *)B, ncols,
-                                  (double2 *)Y, ncols, subtract, (cudaStream_t)stream);
+    cudaError_t e;
+    if (precision == PSEUDO_FP64)
+        e = launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
+                          nullptr, (const double2 *)X, ncols, (const double2 *)B, ncols, (double2 *)Y, ncols, subtract,
+                          (cudaStream_t)stream);
+    else
+        e = launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, nullptr,
+                           (const double2 *)z, (int)ncols, (const double2 *)X, ncols, (const double2 *)B, ncols,
+                           (double2 *)Y, ncols, subtract, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_err(e, "pseudo_matvec");
     h->stats.mv_M += ncols;
     return PSEUDO_OK;
@@ -303,8 +332,16 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     io.on_host = o->io_host != 0;
     Carver c((char *)workspace, workspace_bytes);
     cudaStream_t s = (cudaStream_t)stream;
-    if (o->mode == PSEUDO_INVLANC) return invlanc_run(h, o, io, c, s);
-    return recycle_run(h, o, io, c, s);
+    h->prof = o->profile != 0;
+    h->recs.clear();
+    h->evn = 0;
+    const int res = o->mode == PSEUDO_INVLANC ? invlanc_run(h, o, io, c, s) : recycle_run(h, o, io, c, s);
+    if (h->prof) {
+        cudaStreamSynchronize(s);
+        kp_resolve(h);
+        h->prof = false;
+    }
+    return res;
 }
 
 }  // extern "C"

@@ -101,11 +101,9 @@ __global__ void upd_shift_k_kernel(double2 *__restrict__ H1, double2 *__restrict
         for (int q = 0; q < 3; ++q) {
             // move rows/cols [lb, k) to [0, kn): ascending order, one pass per row
             for (int a = 0; a < kn; ++a) {
-                for (int b = threadIdx.x; b < kn; b += blockDim.x) {
-                    const double2 v = M[q][(a + lb) * KM + b + lb];
-                    __syncwarp();
-                    M[q][a * KM + b] = v;
-                }
+                // source row a + lb and destination row a differ, so each thread
+                // can move its elements without waiting on the others
+                for (int b = threadIdx.x; b < kn; b += blockDim.x) M[q][a * KM + b] = M[q][(a + lb) * KM + b + lb];
                 __syncthreads();
             }
             for (int e = threadIdx.x; e < KM * KM; e += blockDim.x) {
@@ -116,11 +114,7 @@ __global__ void upd_shift_k_kernel(double2 *__restrict__ H1, double2 *__restrict
         }
         double2 *Cu = C + (int64_t)u * KM * r;
         for (int a = 0; a < kn; ++a) {
-            for (int c = threadIdx.x; c < r; c += blockDim.x) {
-                const double2 v = Cu[(a + lb) * r + c];
-                __syncwarp();
-                Cu[a * r + c] = v;
-            }
+            for (int c = threadIdx.x; c < r; c += blockDim.x) Cu[a * r + c] = Cu[(a + lb) * r + c];
             __syncthreads();
         }
         for (int e = threadIdx.x; e < KM * r; e += blockDim.x)
@@ -351,36 +345,36 @@ __global__ void copy_block_kernel(TSView src, TSView dst, int n, int kc, const i
 
 // ------------------------------------------------------------ launchers
 void launch_small_matmul(const double2 *A, const double2 *B, double2 *C, int m, int nitems, cudaStream_t s) {
-    if (nitems > 0) small_matmul_kernel<<<nitems, 64, 0, s>>>(A, B, C, m);
+    if (nitems > 0) { note_launch(); small_matmul_kernel<<<nitems, 64, 0, s>>>(A, B, C, m); }
 }
 void launch_copy_block(TSView src, TSView dst, int n, int kc, int nitems, const int *items, cudaStream_t s) {
     if (nitems <= 0 || kc <= 0) return;
     dim3 g(64, nitems);
-    copy_block_kernel<<<g, 256, 0, s>>>(src, dst, n, kc, items);
+    note_launch(); copy_block_kernel<<<g, 256, 0, s>>>(src, dst, n, kc, items);
 }
 void launch_upd_decide(const int *lanes, int nu, int *p, int r, int KM, int p_max, double omega, const double2 *C,
                        const double2 *gx, int *lout, int *kk, int *nskip, cudaStream_t s) {
-    if (nu > 0) upd_decide_kernel<<<nu, 32, 0, s>>>(lanes, p, r, KM, p_max, omega, C, gx, lout, kk, nskip);
+    if (nu > 0) { note_launch(); upd_decide_kernel<<<nu, 32, 0, s>>>(lanes, p, r, KM, p_max, omega, C, gx, lout, kk, nskip); }
 }
 void launch_upd_shift(double2 *V, double2 *W1, double2 *W3, double2 *W4, int n, int64_t ld, double2 *H1, double2 *H2,
                       double2 *Lf, double2 *C, int KM, int r, const int *lanes, int nu, int *p, const int *lout,
                       cudaStream_t s) {
     if (nu <= 0) return;
     dim3 g((n + 127) / 128, nu);
-    upd_shift_n_kernel<<<g, 128, 0, s>>>(V, W1, W3, W4, n, ld, KM, r, lanes, p, lout);
-    upd_shift_k_kernel<<<nu, 256, 0, s>>>(H1, H2, Lf, C, KM, r, lanes, p, lout);
+    note_launch(); upd_shift_n_kernel<<<g, 128, 0, s>>>(V, W1, W3, W4, n, ld, KM, r, lanes, p, lout);
+    note_launch(); upd_shift_k_kernel<<<nu, 256, 0, s>>>(H1, H2, Lf, C, KM, r, lanes, p, lout);
 }
 void launch_upd_chol(const double2 *G, int r, int nu, const int *lout, double2 *R, double2 *Ri, cudaStream_t s) {
-    if (nu > 0) upd_chol_kernel<<<nu, UP_THREADS, 0, s>>>(G, r, lout, R, Ri);
+    if (nu > 0) { note_launch(); upd_chol_kernel<<<nu, UP_THREADS, 0, s>>>(G, r, lout, R, Ri); }
 }
 void launch_upd_add(double2 *U, const double2 *U2, int cnt, int nu, cudaStream_t s) {
-    if (nu > 0) upd_add_kernel<<<nu, 128, 0, s>>>(U, U2, cnt);
+    if (nu > 0) { note_launch(); upd_add_kernel<<<nu, 128, 0, s>>>(U, U2, cnt); }
 }
 void launch_upd_rotate(double2 *H1, double2 *H2, double2 *Lf, double2 *Qacc, const double2 *U, const double2 *Rnew,
                        const double2 *Hc1, const double2 *Hc2, const double2 *Hr2, int KM, int r, const int *lanes,
                        int nu, int *p, const int *kk, cudaStream_t s) {
     if (nu > 0)
-        upd_rotate_kernel<<<nu, UP_THREADS, 0, s>>>(H1, H2, Lf, Qacc, U, Rnew, Hc1, Hc2, Hr2, KM, r, lanes, p, kk);
+        note_launch(); upd_rotate_kernel<<<nu, UP_THREADS, 0, s>>>(H1, H2, Lf, Qacc, U, Rnew, Hc1, Hc2, Hr2, KM, r, lanes, p, kk);
 }
 
 }  // namespace pseudo

@@ -14,6 +14,8 @@
 //      polished by one step of inverse iteration with FP64-corrected solves,
 //   4. updateRecy is applied per lane, in the lane's visiting order.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <vector>
 
@@ -287,12 +289,15 @@ static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int poli
             for (int it = 0; it < max_ir; ++it) {
                 launch_colnorm2(R.R64, n, cnt, nullptr, R.rn2, s);
                 launch_scale_to32(R.R64, n, cnt, nullptr, R.rn2, R.D32, s);
+                int k0 = kp_begin(h, s);
                 e = launch_trsv32(lower ? h->L32 : h->U32, n, h->n_pad, lower, nullptr, R.zc, cnt, nullptr, R.D32, cnt,
                                   (float2 *)R.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, cnt), tri_bytes(n, cnt, 8, 8, 2), s);
                 if (e != cudaSuccess) return e;
                 launch_acc_from32(R.X64, n, cnt, nullptr, R.rn2, R.D32, s);
-                e = launch_trmv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, nullptr, R.zc, cnt, nullptr, R.X64, cnt, B,
-                                  cnt, R.R64, cnt, 1, s);
+                k0 = kp_begin(h, s);
+                e = trmv_hp(h, true, lower, nullptr, R.zc, cnt, R.X64, cnt, B, cnt, R.R64, cnt, 1, s);
+                kp_end(h, k0, PSEUDO_K_TRMV_DS, tri_flops(n, cnt), tri_bytes(n, cnt, 16, 16, 3), s);
                 if (e != cudaSuccess) return e;
                 h->stats.sv_R += cnt;
                 h->stats.mv_M_fp64_refine += cnt;
@@ -301,8 +306,10 @@ static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int poli
         launch_normalize(R.X64, n, cnt, nullptr, s);
         cudaMemcpyAsync(R.U, R.X64, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
-    launch_trmv64(h->U64, n, h->n_pad, 0, nullptr, R.zc, cnt, nullptr, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s);
-    launch_trmv64(h->L64, n, h->n_pad, 1, nullptr, R.zc, cnt, nullptr, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s);
+    int k1 = kp_begin(h, s);
+    trmv_hp(h, R.fp32, 0, nullptr, R.zc, cnt, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s);
+    trmv_hp(h, R.fp32, 1, nullptr, R.zc, cnt, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s);
+    kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 2 * tri_flops(n, cnt), 2 * tri_bytes(n, cnt, 16, 16, 2), s);
     h->stats.mv_M_fp64_refine += 2 * (int64_t)cnt;
     launch_rq_residual(R.U, R.Y, R.NX, n, cnt, nullptr, R.s2, R.rr, s);
     return cudaGetLastError();
@@ -316,12 +323,17 @@ static cudaError_t solve_listed(pseudo_ctx *h, RecyLayout &R, double2 *buf, int 
     if (ncols <= 0) return cudaSuccess;
     const int n = h->n, r3 = 3 * R.r;
     if (!R.fp32) {
-        return launch_trsv64(adjoint ? h->L64 : h->U64, n, h->n_pad, adjoint, R.cols, R.zcol, ncols, nullptr, buf, R.Wd,
-                             (double2 *)R.xs, s);
+        const int k0 = kp_begin(h, s);
+        cudaError_t e = launch_trsv64(adjoint ? h->L64 : h->U64, n, h->n_pad, adjoint, R.cols, R.zcol, ncols, nullptr,
+                                      buf, R.Wd, (double2 *)R.xs, s);
+        kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncols), tri_bytes(n, ncols, 16, 16, 2), s);
+        return e;
     }
     launch_copy_listed<double2, float2>(buf, R.SB32, n, R.Wd, R.cols, ncols, 0, 0, r3, scale, LB_MAXM, 1, s);
+    const int k0 = kp_begin(h, s);
     cudaError_t e = launch_trsv32(adjoint ? h->L32 : h->U32, n, h->n_pad, adjoint, R.cols, R.zcol, ncols, nullptr,
                                   R.SB32, R.Wd, (float2 *)R.xs, s);
+    kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncols), tri_bytes(n, ncols, 8, 8, 2), s);
     if (e != cudaSuccess) return e;
     launch_copy_listed<float2, double2>(R.SB32, buf, n, R.Wd, R.cols, ncols, 0, 0, r3, scale, LB_MAXM, 0, s);
     return cudaGetLastError();
@@ -504,10 +516,13 @@ static int update_slot(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, const
     launch_ts_mul(X2, r, R.R2i, (int64_t)r * r, Vnew, r, n, nu, nullptr, 0.0, 1.0, s);
     launch_small_matmul(R.R2, R.Rn, R.Rf, r, nu, s);
     // W1+ = T V+, W4+ = T^H V+, W3+ = T^H W1+  (3r products with M per update)
-    lane_cols_kernel<<<(nu * r + 127) / 128, 128, 0, s>>>(R.slot_lanes, R.kk, nu, r, KM, R.ucols);
-    launch_trmv64(h->U64, n, h->n_pad, 0, R.ucols, nullptr, nu * r, nullptr, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s);
-    launch_trmv64(h->L64, n, h->n_pad, 1, R.ucols, nullptr, nu * r, nullptr, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s);
-    launch_trmv64(h->L64, n, h->n_pad, 1, R.ucols, nullptr, nu * r, nullptr, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s);
+    note_launch(); lane_cols_kernel<<<(nu * r + 127) / 128, 128, 0, s>>>(R.slot_lanes, R.kk, nu, r, KM, R.ucols);
+    const int k1 = kp_begin(h, s);
+    trmv_hp(h, R.fp32, 0, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s);
+    kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 3 * tri_flops(n, nu * r),
+           3 * tri_bytes(n, nu * r, 16, 16, 2), s);
     h->stats.mv_M += 3 * (int64_t)nu * r;
     // new blocks of H1 = W1^H W1 and H2 = W1^H V
     launch_ts_gram(W1l, KM, W1new, r, n, nu, nullptr, R.Hc1, (int64_t)KM * r, true, s);
@@ -573,6 +588,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     std::vector<int64_t> pos(seg.begin(), seg.end() - 1);
     std::vector<int> started(R.L, 0);
     const double eps_shift = o->eps_shift_rel * h->norm2 * h->norm2;
+    const bool trace = getenv("PSEUDO_TRACE") != nullptr;  // per-round progress on stderr
     int64_t n_acc = 0, n_ref = 0;
     std::vector<int> gidx_r, lane_r, acc_h, items_h;
     for (int round = 0;; ++round) {
@@ -588,7 +604,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         if (np == 0) break;
         cudaMemcpyAsync(R.ridx, gidx_r.data(), np * sizeof(int), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(R.lane_r, lane_r.data(), np * sizeof(int), cudaMemcpyHostToDevice, s);
-        gather_z_kernel<<<(np + 127) / 128, 128, 0, s>>>(zall, R.ridx, np, R.zr);
+        note_launch(); gather_z_kernel<<<(np + 127) / 128, 128, 0, s>>>(zall, R.ridx, np, R.zr);
         // 1. recySing for every point of the round
         RecySingLaunch rs;
         rs.n = n; rs.KM = R.KM; rs.r = R.r; rs.npts = np; rs.ldv = R.Ld;
@@ -597,11 +613,20 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         rs.eps_shift = eps_shift; rs.tau = o->tau; rs.eta = o->eta; rs.rtol = o->rtol; rs.norm2 = h->norm2;
         rs.sigma = R.sig_r; rs.res = R.res_r; rs.xi2 = R.xi2_r; rs.w2 = R.w2_r; rs.accept = R.acc_r; rs.rt = R.rt_r;
         rs.CX = R.CX;
-        if ((e = launch_recysing(rs, s)) != cudaSuccess) return cuda_err(e, "recySing");
+        {
+            const int k0 = kp_begin(h, s);
+            e = launch_recysing(rs, s);
+            // per point: Y and its Gram (2k r + r^2 complex MACs per row, r = block size as a floor for r~),
+            // two residual columns (8k per row), the k x k Jacobi (~9 k^3 real)
+            const double kf = R.KM, rf = R.r;
+            kp_end(h, k0, PSEUDO_K_RECYSING, np * (8.0 * n * (2 * kf * rf + rf * rf + 8 * kf) + 9 * kf * kf * kf),
+                   (double)R.L * 4.0 * n * kf * 16.0, s);
+            if (e != cudaSuccess) return cuda_err(e, "recySing");
+        }
         acc_h.assign(np, 0);
         cudaMemcpyAsync(acc_h.data(), R.acc_r, np * sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "recySing");
-        scatter_round_kernel<<<(np + 127) / 128, 128, 0, s>>>(nullptr, np, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_ACCEPTED,
+        note_launch(); scatter_round_kernel<<<(np + 127) / 128, 128, 0, s>>>(nullptr, np, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_ACCEPTED,
                                                               R.eps, io.neps, sig_all, res_all, flags_all, member_all,
                                                               nullptr);
         items_h.clear();
@@ -625,21 +650,25 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             if (!cold.empty()) {
                 cudaMemcpyAsync(R.items, cold.data(), cold.size() * sizeof(int), cudaMemcpyHostToDevice, s);
                 dim3 g(32, (unsigned)cold.size());
-                rand_block_kernel<<<g, 256, 0, s>>>(R.S, n, R.Wd, R.r, R.items, (int)cold.size(), R.ridx,
+                note_launch(); rand_block_kernel<<<g, 256, 0, s>>>(R.S, n, R.Wd, R.r, R.items, (int)cold.size(), R.ridx,
                                                     o->seed + 7919ull * round);
             }
         }
+        const int64_t it0 = h->stats.lobpcg_iters;
         const int nbad = lobpcg_refine(h, o, R, nr, items_h, s);
+        if (trace)
+            fprintf(stderr, "[pseudo] round %d: %d points, %d refined, %lld LOBPCG iterations, %d unconverged\n", round,
+                    np, nr, (long long)(h->stats.lobpcg_iters - it0), nbad);
         if (nbad < 0) return nbad;
         // 3. sigma and residual of the refined points (polished in mixed precision)
         cudaMemcpyAsync(R.items, items_h.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s);
-        x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 0);
+        note_launch(); x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 0);
         launch_normalize(R.U, n, nr, nullptr, s);
         if ((e = polish_and_rq(h, R, nr, R.fp32 ? 1 : 0, o->max_ir, s)) != cudaSuccess) return cuda_err(e, "polish");
-        if (R.fp32) x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 1);
-        refined_values_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.xi, R.s2, R.rr, R.zr, h->norm2,
+        if (R.fp32) { note_launch(); x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 1); }
+        note_launch(); refined_values_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.xi, R.s2, R.rr, R.zr, h->norm2,
                                                                R.fp32 ? 1 : 0, R.sig_r, R.res_r);
-        scatter_round_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_REFINED,
+        note_launch(); scatter_round_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_REFINED,
                                                               R.eps, io.neps, sig_all, res_all, flags_all, member_all,
                                                               R.nflag);
         // 4. updateRecy per lane in visiting order: slot u = the u-th refined point of each lane

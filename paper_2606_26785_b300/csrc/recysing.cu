@@ -243,7 +243,7 @@ cudaError_t launch_recysing(const RecySingLaunch &L, cudaStream_t s) {
     a.sigma = L.sigma; a.res = L.res; a.xi2 = L.xi2; a.w2 = L.w2; a.accept = L.accept; a.rt = L.rt; a.CX = L.CX;
     const size_t sm = recysing_smem(L.KM);
     cudaFuncSetAttribute(recysing_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    recysing_kernel<<<L.npts, RS_THREADS, sm, s>>>(a);
+    note_launch(); recysing_kernel<<<L.npts, RS_THREADS, sm, s>>>(a);
     return cudaGetLastError();
 }
 

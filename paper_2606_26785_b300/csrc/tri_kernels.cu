@@ -51,8 +51,8 @@ void launch_pack_panels(const double2 *T, int64_t ldT, int n, int n_pad, double2
     int64_t tot = (int64_t)n_pad * n_pad;
     int th = 256;
     int64_t bl = (tot + th - 1) / th;
-    pack_panels_kernel<double><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U64, L64);
-    pack_panels_kernel<float><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U32, L32);
+    note_launch(); pack_panels_kernel<double><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U64, L64);
+    note_launch(); pack_panels_kernel<float><<<(unsigned)bl, th, 0, s>>>(T, ldT, n, n_pad, U32, L32);
 }
 
 // ------------------------------------------------------------------ solve
@@ -218,7 +218,7 @@ static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower
     }
     int grid = (ncols + R - 1) / R;
     if (grid == 0) return cudaSuccess;
-    trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs);
+    note_launch(); trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs);
     return cudaGetLastError();
 }
 
@@ -315,9 +315,143 @@ cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const 
                           int64_t ldb, double2 *Y, int64_t ldy, int subtract, cudaStream_t s) {
     if (ncols <= 0) return cudaSuccess;
     dim3 grid(n_pad / PH, (ncols + RMV - 1) / RMV);
-    trmv_ms_kernel<RMV, NW_MV><<<grid, NW_MV * 32, 0, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx,
+    note_launch(); trmv_ms_kernel<RMV, NW_MV><<<grid, NW_MV * 32, 0, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx,
                                                            B, ldb, Y, ldy, subtract);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------- double-single product
+// y_c = b_c - (T - z_c I)^{op} x_c (or without b) with T held as two FP32
+// planes (T = T_hi + T_lo to 48 bits) and every product and sum carried in
+// double-single arithmetic (Dekker's exact product through FMA and Knuth's
+// two-sum), so that the FP32 pipes, 62x faster than FP64 on this GPU, give
+// a result with relative error about 2^-46 instead of FP32's 2^-24.
+struct dsf {
+    float hi, lo;
+};
+__device__ __forceinline__ void ds_acc(dsf &s, float a_hi, float a_lo, float b_hi, float b_lo) {
+    // s += a * b with a = a_hi + a_lo, b = b_hi + b_lo (a_lo * b_lo dropped)
+    const float p = a_hi * b_hi;
+    float e = fmaf(a_hi, b_hi, -p);
+    e = fmaf(a_hi, b_lo, e);
+    e = fmaf(a_lo, b_hi, e);
+    const float t = s.hi + p;
+    const float bp = t - s.hi;
+    const float err = (s.hi - (t - bp)) + (p - bp);
+    s.hi = t;
+    s.lo += err + e;
+}
+__device__ __forceinline__ double ds_val(dsf s) { return (double)s.hi + (double)s.lo; }
+__device__ __forceinline__ void ds_norm(dsf &s) {
+    const float t = s.hi + s.lo;
+    s.lo = s.lo - (t - s.hi);
+    s.hi = t;
+}
+
+template <int R, int NW>
+__global__ void __launch_bounds__(NW * 32)
+trmv_ds_kernel(const float2 *__restrict__ Ph, const float2 *__restrict__ Pl, int n, int n_pad, int lower,
+               const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols,
+               const double2 *__restrict__ X, int64_t ldx, const double2 *__restrict__ B, int64_t ldb,
+               double2 *__restrict__ Y, int64_t ldy, int subtract) {
+    __shared__ double2 red[NW][PH][R];
+    __shared__ int s_col[R];
+    __shared__ double2 s_z[R];
+    const int P = blockIdx.x, g = blockIdx.y;
+    if (g * R >= ncols) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < R) {
+        int pos = g * R + threadIdx.x;
+        int c = -1;
+        double2 z = make_double2(0.0, 0.0);
+        if (pos < ncols) { c = cols ? cols[pos] : pos; if (zc) z = zc[c]; }
+        if (lower) z.y = -z.y;
+        s_col[threadIdx.x] = c;
+        s_z[threadIdx.x] = z;
+    }
+    __syncthreads();
+    const int64_t off = lower ? lower_panel_offset(P) : upper_panel_offset(P, n_pad);
+    const float2 *ph = Ph + off, *pl = Pl + off;
+    const int kp1 = lower ? (P + 1) * PH / 2 : (n_pad - P * PH) / 2;
+    const int kcol0 = lower ? 0 : P * PH;
+    dsf ar[2][R], ai[2][R];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < R; ++c) { ar[q][c] = dsf{0.f, 0.f}; ai[q][c] = dsf{0.f, 0.f}; }
+    const int per = (kp1 + NW - 1) / NW;
+    const int a = warp * per, b = min(kp1, a + per);
+    for (int kp = a; kp < b; ++kp) {
+        const int64_t to = (int64_t)kp * (2 * PH) + 2 * lane;
+        float2 th[2][2], tl[2][2];
+        th[0][0] = ph[to]; th[0][1] = ph[to + 1]; th[1][0] = ph[to + 64]; th[1][1] = ph[to + 65];
+        tl[0][0] = pl[to]; tl[0][1] = pl[to + 1]; tl[1][0] = pl[to + 64]; tl[1][1] = pl[to + 65];
+        const int k0 = kcol0 + 2 * kp;
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+            const int cc = s_col[c];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                double2 xv = make_double2(0.0, 0.0);
+                if (cc >= 0 && k0 + u < n) xv = X[(int64_t)(k0 + u) * ldx + cc];
+                const float xrh = (float)xv.x, xih = (float)xv.y;
+                const float xrl = (float)(xv.x - (double)xrh), xil = (float)(xv.y - (double)xih);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float2 h = th[q][u], l = tl[q][u];
+                    // re += t.re x.re - t.im x.im ; im += t.re x.im + t.im x.re
+                    ds_acc(ar[q][c], h.x, l.x, xrh, xrl);
+                    ds_acc(ar[q][c], -h.y, -l.y, xih, xil);
+                    ds_acc(ai[q][c], h.x, l.x, xih, xil);
+                    ds_acc(ai[q][c], h.y, l.y, xrh, xrl);
+                }
+            }
+        }
+        // renormalise (fast two-sum) so that |lo| stays within an ulp of hi
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = 0; c < R; ++c) {
+                ds_norm(ar[q][c]);
+                ds_norm(ai[q][c]);
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < R; ++c) red[warp][lane + 32 * q][c] = make_double2(ds_val(ar[q][c]), ds_val(ai[q][c]));
+    __syncthreads();
+    for (int e = threadIdx.x; e < PH * R; e += NW * 32) {
+        const int li = e / R, c = e % R, row = P * PH + li, cc = s_col[c];
+        if (row >= n || cc < 0) continue;
+        double2 y = make_double2(0.0, 0.0);
+        for (int w = 0; w < NW; ++w) y = cadd(y, red[w][li][c]);
+        const double2 xr = X[(int64_t)row * ldx + cc];
+        cfms(y, s_z[c], xr);
+        if (subtract) y = csub(B[(int64_t)row * ldb + cc], y);
+        Y[(int64_t)row * ldy + cc] = y;
+    }
+}
+
+constexpr int RDS = 4, NW_DS = 8;
+cudaError_t launch_trmv_ds(const float2 *Ph, const float2 *Pl, int n, int n_pad, int lower, const int *cols,
+                           const double2 *zc, int ncols, const double2 *X, int64_t ldx, const double2 *B, int64_t ldb,
+                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s) {
+    if (ncols <= 0) return cudaSuccess;
+    dim3 grid(n_pad / PH, (ncols + RDS - 1) / RDS);
+    note_launch(); trmv_ds_kernel<RDS, NW_DS><<<grid, NW_DS * 32, 0, s>>>(Ph, Pl, n, n_pad, lower, cols, zc, ncols, X, ldx, B, ldb, Y,
+                                                            ldy, subtract);
+    return cudaGetLastError();
+}
+
+// low FP32 plane: fl32(T - fl32(T)) in the same packed layout
+__global__ void pack_lo_kernel(const double2 *__restrict__ P64, const float2 *__restrict__ P32, float2 *__restrict__ Plo,
+                               int64_t cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        Plo[i] = make_float2((float)(P64[i].x - (double)P32[i].x), (float)(P64[i].y - (double)P32[i].y));
+}
+void launch_pack_lo(const double2 *P64, const float2 *P32, float2 *Plo, int64_t cnt, cudaStream_t s) {
+    note_launch(); pack_lo_kernel<<<1184, 256, 0, s>>>(P64, P32, Plo, cnt);
 }
 
 // ------------------------------------------------------------------ norms
@@ -338,7 +472,7 @@ __global__ void sumsq_kernel(const double2 *__restrict__ a, int64_t cnt, double 
 
 cudaError_t launch_sumsq(const double2 *a, int64_t cnt, double *out, cudaStream_t s) {
     cudaMemsetAsync(out, 0, sizeof(double), s);
-    sumsq_kernel<<<296, 256, 0, s>>>(a, cnt, out);
+    note_launch(); sumsq_kernel<<<296, 256, 0, s>>>(a, cnt, out);
     return cudaGetLastError();
 }
 
@@ -350,7 +484,7 @@ __global__ void extract_diag_kernel(const double2 *__restrict__ U, int n, int n_
 }
 
 cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, cudaStream_t s) {
-    extract_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(U, n, n_pad, d);
+    note_launch(); extract_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(U, n, n_pad, d);
     return cudaGetLastError();
 }
 

@@ -88,7 +88,7 @@ cudaError_t launch_ts_gram(TSView A, int ka, TSView B, int kb, int n, int nitems
         attr = true;
     }
     dim3 grid(nitems, (n + slice - 1) / slice);
-    ts_gram_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, B, kb, n, items, G, gstride, slice);
+    note_launch(); ts_gram_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, B, kb, n, items, G, gstride, slice);
     return cudaGetLastError();
 }
 
@@ -102,7 +102,7 @@ cudaError_t launch_ts_mul(TSView A, int ka, const double2 *C, int64_t cstride, T
         attr = true;
     }
     dim3 grid(nitems, (n + TS_ROWS - 1) / TS_ROWS);
-    ts_mul_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, C, cstride, O, kb, n, items, beta, alpha);
+    note_launch(); ts_mul_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, C, cstride, O, kb, n, items, beta, alpha);
     return cudaGetLastError();
 }
 

@@ -31,11 +31,11 @@ def test_struct_layout_matches_header(tmp_path):
 
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pseudo.h"\nint main(){printf("%zu %zu %zu %zu",'
-                   'sizeof(pseudo_opts),sizeof(pseudo_stats_t),offsetof(pseudo_opts,seed),offsetof(pseudo_stats_t,ms_total));}')
+                   'sizeof(pseudo_opts),sizeof(pseudo_stats_t),offsetof(pseudo_opts,profile),offsetof(pseudo_stats_t,ms_total));}')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()
-    assert [int(v) for v in out] == [ctypes.sizeof(_abi.Opts), ctypes.sizeof(_abi.Stats), _abi.Opts.seed.offset,
+    assert [int(v) for v in out] == [ctypes.sizeof(_abi.Opts), ctypes.sizeof(_abi.Stats), _abi.Opts.profile.offset,
                                      _abi.Stats.ms_total.offset]
 
 

@@ -62,6 +62,28 @@ def test_matvec_fp64(n, adjoint):
     h.close()
 
 
+@pytest.mark.parametrize("n", [3, 65, 257])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_matvec_double_single(n, adjoint):
+    """double-single product: relative error near 2^-46, far below FP32's."""
+    import torch
+
+    import paper_2606_26785_b300 as p
+
+    T, z, B = _case(n, 6, 11 + n)
+    rng = np.random.default_rng(n + 1)
+    X = rng.standard_normal((n, 6)) + 1j * rng.standard_normal((n, 6))
+    h = p.Pseudo(T)
+    Xt, Bt = torch.from_numpy(X).cuda(), torch.from_numpy(B).cuda()
+    ref = steps.shifted_matvec(T, z, X, adjoint)
+    Y = h.matvec(Xt, z=z, adjoint=adjoint, precision=p.MIXED).cpu().numpy()
+    scale = np.abs(np.triu(T)).sum(axis=1 if not adjoint else 0).max() * np.abs(X).max() + 1
+    assert np.max(np.abs(Y - ref)) <= 64 * n * 2.0 ** -46 * scale
+    R = h.matvec(Xt, z=z, B=Bt, adjoint=adjoint, precision=p.MIXED).cpu().numpy()
+    assert np.max(np.abs(R - (B - ref))) <= 64 * n * 2.0 ** -46 * scale
+    h.close()
+
+
 def test_norms():
     import paper_2606_26785_b300 as p
 
