@@ -79,7 +79,8 @@ typedef struct {
     int grid_nx, grid_ny; /* Cartesian layout of z[] (row-major, x fastest); 0 = unordered */
     int batch_b;        /* column-batch size b of the batch-zigzag traversal (paper 20) */
     int lanes;          /* independent recycle lanes processed side by side (0 = auto) */
-    int shift_batch;    /* INVLANC: shifts per launch wave (0 = auto) */
+    int shift_batch;    /* INVLANC: shifts per launch wave (0 = auto); RECYCLE: points each lane
+                           takes per round (0 = 1: V is updated after every refined point) */
     double eps_shift_rel; /* epsilon = eps_shift_rel * ||T||_2^2 (paper 1e-14) */
     double tau;         /* eigen-gap tolerance of eq. (tau) (paper 1e-10) */
     double omega;       /* pruning threshold of eq. (omegaCond) (paper 1.6) */
@@ -205,6 +206,7 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
                  int precision, void *workspace, size_t workspace_bytes, void *stream);
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
                   const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision, void *stream);
+
 
 #ifdef __cplusplus
 }

@@ -106,13 +106,36 @@ namespace pseudo {
 // (T - zI)^{op} products for the refinement residuals and the recycled
 // subspace: IEEE FP64 in FP64 mode, double-single on the FP32 units in mixed
 // mode.
+// xh / xl: scratch with X's layout (leading dimension ldx) for the FP32 split
+// of X used by the double-single kernel.
 inline cudaError_t trmv_hp(pseudo_ctx *h, bool ds, int lower, const int *cols, const double2 *zc, int ncols,
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
-                           int subtract, cudaStream_t s) {
+                           int subtract, cudaStream_t s, float2 *xh = nullptr, float2 *xl = nullptr) {
     if (ds)
         return launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, cols, zc,
-                              ncols, X, ldx, B, ldb, Y, ldy, subtract, s);
+                              ncols, X, ldx, B, ldb, Y, ldy, subtract, s, xh, xl);
     return launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, cols, zc, ncols, nullptr, X, ldx, B, ldb, Y,
                          ldy, subtract, s);
 }
 }  // namespace pseudo
+
+namespace pseudo {
+// refine.cu: iterative refinement of shifted solves (mixed precision)
+struct IRBufs {
+    double2 *R64;     // residuals, n x S
+    float2 *D32;      // FP32 right-hand sides / corrections, n x S
+    double *rn2;      // per-column squared residual norms
+    int *mask, *need, *perm;
+    float2 *xs;       // FP32 solve scratch for S columns
+    float2 *xh, *xl;  // double-single split of X, n x S
+};
+struct IRPlan {
+    std::vector<int> cnt;  // cnt[it]: columns still refining at step it
+};
+// need[c] for c < sig.size(), zero for the other columns up to S_total
+void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<double2> &z, int max_ir,
+             const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total = 0);
+cudaError_t ir_solve_cols(pseudo_ctx *h, const IRBufs &b, int lower, const double2 *zc, int S, const double2 *B,
+                          double2 *X, const IRPlan &plan, cudaStream_t s);
+}  // namespace pseudo
+

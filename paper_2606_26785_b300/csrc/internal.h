@@ -21,7 +21,8 @@ cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const 
                           int64_t ldb, double2 *Y, int64_t ldy, int subtract, cudaStream_t s);
 cudaError_t launch_trmv_ds(const float2 *Ph, const float2 *Pl, int n, int n_pad, int lower, const int *cols,
                            const double2 *zc, int ncols, const double2 *X, int64_t ldx, const double2 *B, int64_t ldb,
-                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s);
+                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s, float2 *Xh = nullptr,
+                           float2 *Xl = nullptr);
 void launch_pack_lo(const double2 *P64, const float2 *P32, float2 *Plo, int64_t cnt, cudaStream_t s);
 cudaError_t launch_sumsq(const double2 *a, int64_t cnt, double *out, cudaStream_t s);
 cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, cudaStream_t s);
@@ -103,4 +104,25 @@ void launch_upd_rotate(double2 *H1, double2 *H2, double2 *Lf, double2 *Qacc, con
                        int nu, int *p, const int *kk, cudaStream_t s);
 void launch_small_matmul(const double2 *A, const double2 *B, double2 *C, int m, int nitems, cudaStream_t s);
 void launch_copy_block(TSView src, TSView dst, int n, int kc, int nitems, const int *items, cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+// lanczos.cu: continuous batching (per-slot steps, refill on convergence)
+template <typename real>
+void launch_slot_copy(const cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, const int *active,
+                      cudaStream_t s);
+template <typename real>
+void launch_slot_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, int mmax,
+                      const int *active, double *alpha, double *beta, int passes, cudaStream_t s);
+void launch_slot_tridiag(int S, int mmax, const double *alpha, const double *beta, int *active, int *jv, double *theta,
+                         double *svec, int *convd, double tol_q, double tol_floor, cudaStream_t s);
+template <typename real>
+void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
+                         const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
+                         int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
+                         int *fin_conv, const double2 *v0, cudaStream_t s);
+void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
+                        const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
+                        double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
+                        cudaStream_t s);
 }  // namespace pseudo

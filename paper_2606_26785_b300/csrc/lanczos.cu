@@ -94,25 +94,25 @@ lanczos_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restri
     for (int pass = 0; pass < 2; ++pass) {
         // h_t = q_t^H w for t = 0..j, in chunks of TCH vectors; then w -= q_t h_t
         for (int t0 = 0; t0 <= j; t0 += TCH) {
-            double2 acc[TCH];
+            // partial dot products in the vectors' own precision: FP32 vectors
+            // get FP32 arithmetic (the FP64 units are 62x slower on this GPU)
+            C acc[TCH];
 #pragma unroll
-            for (int u = 0; u < TCH; ++u) acc[u] = make_double2(0.0, 0.0);
+            for (int u = 0; u < TCH; ++u) acc[u] = mk<real>(0, 0);
             if (on) {
                 for (int i = warp; i < n; i += ORTH_WARPS) {
                     const C wv = W[(int64_t)i * S + cc];
-                    const double wr = wv.x, wi = wv.y;
 #pragma unroll
                     for (int u = 0; u < TCH; ++u) {
                         if (t0 + u <= j) {
                             const C qv = Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc];
-                            acc[u].x += (double)qv.x * wr + (double)qv.y * wi;
-                            acc[u].y += (double)qv.x * wi - (double)qv.y * wr;
+                            cfma(acc[u], cconj(qv), wv);
                         }
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < TCH; ++u) red[warp][u][lane] = acc[u];
+            for (int u = 0; u < TCH; ++u) red[warp][u][lane] = make_double2((double)acc[u].x, (double)acc[u].y);
             __syncthreads();
             if (warp == 0) {
                 for (int u = 0; u < TCH && t0 + u <= j; ++u) {
@@ -124,34 +124,33 @@ lanczos_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restri
             }
             __syncthreads();
             if (on) {
-                double2 hc[TCH];
+                C hc[TCH];
 #pragma unroll
-                for (int u = 0; u < TCH; ++u) hc[u] = (t0 + u <= j) ? red[0][u][lane] : make_double2(0.0, 0.0);
+                for (int u = 0; u < TCH; ++u)
+                    hc[u] = (t0 + u <= j) ? mk<real>((real)red[0][u][lane].x, (real)red[0][u][lane].y) : mk<real>(0, 0);
                 for (int i = warp; i < n; i += ORTH_WARPS) {
                     C wv = W[(int64_t)i * S + cc];
-                    double wr = wv.x, wi = wv.y;
 #pragma unroll
                     for (int u = 0; u < TCH; ++u) {
                         if (t0 + u <= j) {
                             const C qv = Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc];
-                            wr -= (double)qv.x * hc[u].x - (double)qv.y * hc[u].y;
-                            wi -= (double)qv.x * hc[u].y + (double)qv.y * hc[u].x;
+                            cfms(wv, qv, hc[u]);
                         }
                     }
-                    W[(int64_t)i * S + cc] = mk<real>((real)wr, (real)wi);
+                    W[(int64_t)i * S + cc] = wv;
                 }
             }
             __syncthreads();
         }
     }
     // beta = ||w||, q_{j+1} = w / beta
-    double s = 0.0;
+    real sp = 0;
     if (on)
         for (int i = warp; i < n; i += ORTH_WARPS) {
             const C wv = W[(int64_t)i * S + cc];
-            s += (double)wv.x * wv.x + (double)wv.y * wv.y;
+            sp += wv.x * wv.x + wv.y * wv.y;
         }
-    s_nrm[warp][lane] = s;
+    s_nrm[warp][lane] = (double)sp;
     __syncthreads();
     if (warp == 0) {
         double t = 0.0;
@@ -381,5 +380,289 @@ template void launch_lanczos_orth<float>(float2 *, int64_t, float2 *, int, int, 
 template void launch_lanczos_orth<double>(double2 *, int64_t, double2 *, int, int, int, int, const int *, double *, double *, cudaStream_t);
 template void launch_ritz_vector<float>(const float2 *, int64_t, int, int, int, const double *, const int *, double2 *, const int *, cudaStream_t);
 template void launch_ritz_vector<double>(const double2 *, int64_t, int, int, int, const double *, const int *, double2 *, const int *, cudaStream_t);
+
+}  // namespace pseudo
+
+// ===================== continuous batching (slots refilled on convergence)
+// A wave of S slots runs Lanczos recurrences that start and finish at
+// different global iterations: every slot c carries its own step jv[c].
+// active[c]: 1 running, 2 finished this iteration (to harvest), 3 empty
+// (to fill), 0 idle (no points left).
+namespace pseudo {
+
+// W[:, c] = Q[jv[c]][:, c] for running slots
+template <typename real>
+__global__ void slot_copy_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restrict__ W, int n,
+                                 int S, const int *__restrict__ jv, const int *__restrict__ active) {
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (c >= S || active[c] != 1) return;
+    const cx_t<real> *q = Q + (int64_t)jv[c] * qs;
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5) W[(int64_t)i * S + c] = q[(int64_t)i * S + c];
+}
+
+// Reorthogonalise w against q_0..q_{j_c} (classical Gram-Schmidt, `passes`
+// times), alpha_j = Re(q_j^H w), beta_j = ||w||, q_{j+1} = w / beta.
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+slot_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restrict__ W, int n, int S,
+                 const int *__restrict__ jv, int mmax, const int *__restrict__ active, double *__restrict__ alpha,
+                 double *__restrict__ beta, int passes) {
+    using C = cx_t<real>;
+    __shared__ double2 red[ORTH_WARPS][TCH][32];
+    __shared__ double2 s_hj[32];
+    __shared__ double s_nrm[ORTH_WARPS][32];
+    __shared__ int s_jmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool on = (c < S) && active[c] == 1;
+    const int jc = on ? jv[c] : -1;
+    if (threadIdx.x == 0) s_jmax = -1;
+    if (threadIdx.x < 32) s_hj[threadIdx.x] = make_double2(0.0, 0.0);
+    __syncthreads();
+    if (warp == 0 && on) atomicMax(&s_jmax, jc);
+    __syncthreads();
+    const int jmax = s_jmax;
+    if (jmax < 0) return;
+    const int cc = on ? c : 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        for (int t0 = 0; t0 <= jmax; t0 += TCH) {
+            C acc[TCH];
+#pragma unroll
+            for (int u = 0; u < TCH; ++u) acc[u] = mk<real>(0, 0);
+            if (on && t0 <= jc) {
+                for (int i = warp; i < n; i += ORTH_WARPS) {
+                    const C wv = W[(int64_t)i * S + cc];
+#pragma unroll
+                    for (int u = 0; u < TCH; ++u)
+                        if (t0 + u <= jc) cfma(acc[u], cconj(Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc]), wv);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < TCH; ++u) red[warp][u][lane] = make_double2((double)acc[u].x, (double)acc[u].y);
+            __syncthreads();
+            if (warp == 0) {
+                for (int u = 0; u < TCH; ++u) {
+                    double2 s = make_double2(0.0, 0.0);
+                    for (int w = 0; w < ORTH_WARPS; ++w) { s.x += red[w][u][lane].x; s.y += red[w][u][lane].y; }
+                    red[0][u][lane] = s;
+                    if (on && t0 + u == jc) { s_hj[lane].x += s.x; s_hj[lane].y += s.y; }
+                }
+            }
+            __syncthreads();
+            if (on && t0 <= jc) {
+                C hc[TCH];
+#pragma unroll
+                for (int u = 0; u < TCH; ++u)
+                    hc[u] = (t0 + u <= jc) ? mk<real>((real)red[0][u][lane].x, (real)red[0][u][lane].y) : mk<real>(0, 0);
+                for (int i = warp; i < n; i += ORTH_WARPS) {
+                    C wv = W[(int64_t)i * S + cc];
+#pragma unroll
+                    for (int u = 0; u < TCH; ++u)
+                        if (t0 + u <= jc) cfms(wv, Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc], hc[u]);
+                    W[(int64_t)i * S + cc] = wv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    real sp = 0;
+    if (on)
+        for (int i = warp; i < n; i += ORTH_WARPS) {
+            const C wv = W[(int64_t)i * S + cc];
+            sp += wv.x * wv.x + wv.y * wv.y;
+        }
+    s_nrm[warp][lane] = (double)sp;
+    __syncthreads();
+    if (warp == 0) {
+        double t = 0.0;
+        for (int w = 0; w < ORTH_WARPS; ++w) t += s_nrm[w][lane];
+        s_nrm[0][lane] = sqrt(t);
+    }
+    __syncthreads();
+    const double b = s_nrm[0][lane];
+    if (on) {
+        const double inv = b > 0.0 ? 1.0 / b : 0.0;
+        for (int i = warp; i < n; i += ORTH_WARPS) {
+            const C wv = W[(int64_t)i * S + cc];
+            Q[(int64_t)(jc + 1) * qs + (int64_t)i * S + cc] = mk<real>((real)(wv.x * inv), (real)(wv.y * inv));
+        }
+        if (warp == 0) {
+            alpha[(int64_t)c * mmax + jc] = s_hj[lane].x;
+            beta[(int64_t)c * mmax + jc] = b;
+        }
+    }
+}
+
+// Ritz value after step jv[c]; on convergence (or at the step cap) the slot
+// is marked finished (active = 2), otherwise its step advances.
+__global__ void slot_tridiag_kernel(int S, int mmax, const double *__restrict__ alpha, const double *__restrict__ beta,
+                                    int *__restrict__ active, int *__restrict__ jv, double *__restrict__ theta,
+                                    double *__restrict__ svec, int *__restrict__ convd, double tol_q,
+                                    double tol_floor) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S || active[c] != 1) return;
+    const int j = jv[c], k = j + 1;
+    double a[LANCZOS_MMAX], b[LANCZOS_MMAX], s[LANCZOS_MMAX], wk[5 * LANCZOS_MMAX];
+    for (int i = 0; i < k; ++i) { a[i] = alpha[(int64_t)c * mmax + i]; b[i] = beta[(int64_t)c * mmax + i]; }
+    const double th1 = tridiag_eig(a, b, k, k - 1);
+    const double th2 = k > 1 ? tridiag_eig(a, b, k, k - 2) : 0.0;
+    tridiag_vec(a, b, k, th1, s, wk);
+    const double rb = fabs(b[k - 1] * s[k - 1]);
+    const double gap = fmax(th1 - th2, 1e-300);
+    const double est = rb * rb / (th1 * gap);
+    const bool breakdown = b[k - 1] <= 1e-300 * th1;
+    const bool conv = breakdown || est <= tol_q || rb <= tol_floor * th1;
+    theta[c] = th1;
+    for (int i = 0; i < k; ++i) svec[(int64_t)c * mmax + i] = s[i];
+    if (conv || k == mmax) {
+        active[c] = 2;
+        convd[c] = conv ? 1 : 0;
+    } else {
+        jv[c] = j + 1;
+    }
+}
+
+// Harvest finished slots (Ritz vector into the finished buffer, ld F) and
+// refill finished or empty slots with the next points.
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+slot_harvest_kernel(cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, int mmax, const double *__restrict__ svec,
+                    int *__restrict__ jv, int *__restrict__ active, const double *__restrict__ theta,
+                    const int *__restrict__ convd, int *__restrict__ pt, double2 *__restrict__ zslot,
+                    const double2 *__restrict__ zall, int npts, int *__restrict__ counters, double2 *__restrict__ Ufin,
+                    int F, int *__restrict__ fin_pt, double2 *__restrict__ fin_z, double *__restrict__ fin_theta,
+                    int *__restrict__ fin_conv, const double2 *__restrict__ v0) {
+    __shared__ int s_dest[32], s_next[32], s_state[32];
+    __shared__ int any;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    if (warp == 0) {
+        const int st = c < S ? active[c] : 0;
+        int dest = -1, nxt = -1;
+        if (st == 2) dest = atomicAdd(&counters[1], 1);
+        if (st == 2 || st == 3) nxt = atomicAdd(&counters[0], 1);
+        s_state[lane] = st;
+        s_dest[lane] = dest;
+        s_next[lane] = nxt;
+        if (st >= 2) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (!any) return;
+    const int st = s_state[lane], dest = s_dest[lane], nxt = s_next[lane];
+    if (st == 2) {
+        const int k = jv[c] + 1;
+        for (int i = warp; i < n; i += ORTH_WARPS) {
+            double ur = 0.0, ui = 0.0;
+            for (int t = 0; t < k; ++t) {
+                const double sv = svec[(int64_t)c * mmax + t];
+                const cx_t<real> q = Q[(int64_t)t * qs + (int64_t)i * S + c];
+                ur += sv * (double)q.x;
+                ui += sv * (double)q.y;
+            }
+            Ufin[(int64_t)i * F + dest] = make_double2(ur, ui);
+        }
+        if (warp == 0) {
+            fin_pt[dest] = pt[c];
+            fin_z[dest] = zslot[c];
+            fin_theta[dest] = theta[c];
+            fin_conv[dest] = convd[c];
+        }
+    }
+    __syncthreads();  // every read of slot c's basis is done before the refill overwrites q_0
+    if (st == 2 || st == 3) {
+        if (nxt < npts) {
+            for (int i = warp; i < n; i += ORTH_WARPS)
+                Q[(int64_t)i * S + c] = mk<real>((real)v0[i].x, (real)v0[i].y);
+            if (warp == 0) {
+                pt[c] = nxt;
+                zslot[c] = zall[nxt];
+                jv[c] = 0;
+                active[c] = 1;
+            }
+        } else if (warp == 0) {
+            active[c] = 0;
+        }
+    }
+}
+
+// Results of finished points t < P (sigma from theta or from the Rayleigh
+// quotient s2), scattered to their grid positions.
+__global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const double2 *__restrict__ fin_z,
+                                   const double *__restrict__ fin_theta, const int *__restrict__ fin_conv,
+                                   const double *__restrict__ s2, const double *__restrict__ rr, int use_rq,
+                                   double norm2, const double *__restrict__ eps, int neps, double *__restrict__ sigma_out,
+                                   double *__restrict__ res_out, int32_t *__restrict__ flags_out,
+                                   uint32_t *__restrict__ member_out, int *__restrict__ nbad) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= P) return;
+    const double th = fin_theta[t];
+    const double rq = sqrt(fmax(s2[t], 0.0));
+    const double sig = use_rq ? rq : (th > 0.0 ? 1.0 / sqrt(th) : 0.0);
+    const double2 z = fin_z[t];
+    const double mz = norm2 + sqrt(z.x * z.x + z.y * z.y);
+    const int g = fin_pt[t];
+    int fl = PSEUDO_PT_REFINED;
+    if (!fin_conv[t]) { fl |= PSEUDO_PT_NOT_CONVERGED; atomicAdd(nbad, 1); }
+    sigma_out[g] = sig;
+    if (res_out) res_out[g] = rq > 0.0 ? rr[t] / (rq * mz) : 0.0;
+    if (flags_out) flags_out[g] = fl;
+    if (member_out) {
+        uint32_t m = 0;
+        for (int e = 0; e < neps; ++e) m |= (sig < eps[e] ? 1u : 0u) << e;
+        member_out[g] = m;
+    }
+}
+
+template <typename real>
+void launch_slot_copy(const cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, const int *active,
+                      cudaStream_t s) {
+    note_launch(); slot_copy_kernel<real><<<(S + 31) / 32, 256, 0, s>>>(Q, qs, W, n, S, jv, active);
+}
+template <typename real>
+void launch_slot_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, int mmax,
+                      const int *active, double *alpha, double *beta, int passes, cudaStream_t s) {
+    note_launch(); slot_orth_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, jv, mmax, active, alpha, beta,
+                                                                                 passes);
+}
+void launch_slot_tridiag(int S, int mmax, const double *alpha, const double *beta, int *active, int *jv, double *theta,
+                         double *svec, int *convd, double tol_q, double tol_floor, cudaStream_t s) {
+    note_launch(); slot_tridiag_kernel<<<(S + 63) / 64, 64, 0, s>>>(S, mmax, alpha, beta, active, jv, theta, svec, convd, tol_q,
+                                                                  tol_floor);
+}
+template <typename real>
+void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
+                         const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
+                         int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
+                         int *fin_conv, const double2 *v0, cudaStream_t s) {
+    note_launch(); slot_harvest_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, n, S, mmax, svec, jv, active, theta,
+                                                                                    convd, pt, zslot, zall, npts,
+                                                                                    counters, Ufin, F, fin_pt, fin_z,
+                                                                                    fin_theta, fin_conv, v0);
+}
+void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
+                        const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
+                        double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
+                        cudaStream_t s) {
+    if (P > 0) {
+        note_launch(); fin_scatter_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, fin_pt, fin_z, fin_theta, fin_conv, s2, rr, use_rq, norm2,
+                                                                        eps, neps, sigma_out, res_out, flags_out,
+                                                                        member_out, nbad);
+    }
+}
+template void launch_slot_copy<float>(const float2 *, int64_t, float2 *, int, int, const int *, const int *, cudaStream_t);
+template void launch_slot_copy<double>(const double2 *, int64_t, double2 *, int, int, const int *, const int *, cudaStream_t);
+template void launch_slot_orth<float>(float2 *, int64_t, float2 *, int, int, const int *, int, const int *, double *,
+                                      double *, int, cudaStream_t);
+template void launch_slot_orth<double>(double2 *, int64_t, double2 *, int, int, const int *, int, const int *, double *,
+                                       double *, int, cudaStream_t);
+template void launch_slot_harvest<float>(float2 *, int64_t, int, int, int, const double *, int *, int *, const double *,
+                                         const int *, int *, double2 *, const double2 *, int, int *, double2 *, int,
+                                         int *, double2 *, double *, int *, const double2 *, cudaStream_t);
+template void launch_slot_harvest<double>(double2 *, int64_t, int, int, int, const double *, int *, int *,
+                                          const double *, const int *, int *, double2 *, const double2 *, int, int *,
+                                          double2 *, int, int *, double2 *, double *, int *, const double2 *,
+                                          cudaStream_t);
 
 }  // namespace pseudo

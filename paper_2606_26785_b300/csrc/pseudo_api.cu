@@ -70,7 +70,7 @@ int pseudo_opts_default(pseudo_opts *o) {
     o->rtol = 1e-10;
     o->maxiter_lanczos = 64;
     o->maxiter_lobpcg = 60;
-    o->max_ir = 4;
+    o->max_ir = 6;
     o->seed = 12345;
     return PSEUDO_OK;
 }

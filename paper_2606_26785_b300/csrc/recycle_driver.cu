@@ -136,6 +136,8 @@ struct RecyLayout {
     // polish / residual (compact, up to B columns)
     double2 *U, *Y, *NX, *X64, *R64, *B64, *zc;
     float2 *D32;
+    float2 *xh, *xl;  // FP32 split of a product operand, n x max(B, lanes * k_max)
+    int *need, *perm, *mask;  // refinement plan of the polish
     double *rn2, *s2, *rr;
     // update (slots up to L)
     double2 *Xst, *Xt2, *Cc, *C2, *gx, *Rn, *Rni, *R2, *R2i, *Rf, *Hc1, *Hc2, *Hr2, *Qacc, *Tmp;
@@ -160,7 +162,9 @@ static int auto_lanes(const pseudo_opts *o, int64_t npts) {
 static void recy_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, RecyLayout &R, bool on_host) {
     R.r = o->r;
     R.KM = std::min(o->p_max, RECY_KMAX / o->r) * o->r;  // p_max is capped at RECY_KMAX / r
-    R.b = std::max(1, o->batch_b);
+    // points a lane takes per round: 1 keeps the paper's point-by-point
+    // recycling inside every lane (V updated after each refined point)
+    R.b = o->shift_batch > 0 ? o->shift_batch : 1;
     R.L = auto_lanes(o, npts);
     R.B = R.L * R.b;
     R.Ld = R.L * R.KM;
@@ -212,6 +216,11 @@ static void recy_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     R.B64 = c.get<double2>(n * B);
     R.zc = c.get<double2>(B);
     R.D32 = c.get<float2>(n * B);
+    R.xh = c.get<float2>(n * std::max<size_t>(B, R.Ld));
+    R.xl = c.get<float2>(n * std::max<size_t>(B, R.Ld));
+    R.need = c.get<int>(B);
+    R.perm = c.get<int>(B);
+    R.mask = c.get<int>(B);
     R.rn2 = c.get<double>(B);
     R.s2 = c.get<double>(B);
     R.rr = c.get<double>(B);
@@ -276,39 +285,35 @@ static std::vector<int> batch_zigzag(int64_t npts, int nx, int ny, int b) {
 
 // FP64-corrected inverse-iteration polish of cnt unit vectors U (n x cnt)
 // with shifts zc, followed by the Rayleigh quotient s2 and residual rr.
-static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int polish, int max_ir, cudaStream_t s) {
+static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int polish, int max_ir,
+                                 const std::vector<int> &items_h, cudaStream_t s) {
     const int n = h->n;
     cudaError_t e = cudaSuccess;
     if (polish) {
-        for (int dir = 0; dir < 2; ++dir) {
-            const int lower = dir == 0 ? 1 : 0;
-            const double2 *B = dir == 0 ? R.U : R.B64;
-            if (dir == 1) cudaMemcpyAsync(R.B64, R.X64, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-            cudaMemsetAsync(R.X64, 0, (size_t)n * cnt * sizeof(double2), s);
-            cudaMemcpyAsync(R.R64, B, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-            for (int it = 0; it < max_ir; ++it) {
-                launch_colnorm2(R.R64, n, cnt, nullptr, R.rn2, s);
-                launch_scale_to32(R.R64, n, cnt, nullptr, R.rn2, R.D32, s);
-                int k0 = kp_begin(h, s);
-                e = launch_trsv32(lower ? h->L32 : h->U32, n, h->n_pad, lower, nullptr, R.zc, cnt, nullptr, R.D32, cnt,
-                                  (float2 *)R.xs, s);
-                kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, cnt), tri_bytes(n, cnt, 8, 8, 2), s);
-                if (e != cudaSuccess) return e;
-                launch_acc_from32(R.X64, n, cnt, nullptr, R.rn2, R.D32, s);
-                k0 = kp_begin(h, s);
-                e = trmv_hp(h, true, lower, nullptr, R.zc, cnt, R.X64, cnt, B, cnt, R.R64, cnt, 1, s);
-                kp_end(h, k0, PSEUDO_K_TRMV_DS, tri_flops(n, cnt), tri_bytes(n, cnt, 16, 16, 3), s);
-                if (e != cudaSuccess) return e;
-                h->stats.sv_R += cnt;
-                h->stats.mv_M_fp64_refine += cnt;
+        IRBufs ib{R.R64, R.D32, R.rn2, R.mask, R.need, R.perm, (float2 *)R.xs, R.xh, R.xl};
+        IRPlan plan;
+        {
+            std::vector<double> xi((size_t)R.B * LB_MAXM), sg(cnt);
+            std::vector<double2> zr(R.B), zh(cnt);
+            cudaMemcpyAsync(xi.data(), R.xi, xi.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(zr.data(), R.zr, zr.size() * sizeof(double2), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            for (int t = 0; t < cnt; ++t) {
+                const double x1 = xi[(size_t)items_h[t] * LB_MAXM];
+                sg[t] = x1 > 0.0 ? 1.0 / x1 : 0.0;
+                zh[t] = zr[items_h[t]];
             }
+            ir_plan(h, sg, zh, max_ir, ib, plan, s);
         }
+        if ((e = ir_solve_cols(h, ib, 1, R.zc, cnt, R.U, R.X64, plan, s)) != cudaSuccess) return e;
+        cudaMemcpyAsync(R.B64, R.X64, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+        if ((e = ir_solve_cols(h, ib, 0, R.zc, cnt, R.B64, R.X64, plan, s)) != cudaSuccess) return e;
         launch_normalize(R.X64, n, cnt, nullptr, s);
         cudaMemcpyAsync(R.U, R.X64, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
     int k1 = kp_begin(h, s);
-    trmv_hp(h, R.fp32, 0, nullptr, R.zc, cnt, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s);
-    trmv_hp(h, R.fp32, 1, nullptr, R.zc, cnt, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s);
+    trmv_hp(h, R.fp32, 0, nullptr, R.zc, cnt, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s, R.xh, R.xl);
+    trmv_hp(h, R.fp32, 1, nullptr, R.zc, cnt, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s, R.xh, R.xl);
     kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 2 * tri_flops(n, cnt), 2 * tri_bytes(n, cnt, 16, 16, 2), s);
     h->stats.mv_M_fp64_refine += 2 * (int64_t)cnt;
     launch_rq_residual(R.U, R.Y, R.NX, n, cnt, nullptr, R.s2, R.rr, s);
@@ -518,9 +523,9 @@ static int update_slot(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, const
     // W1+ = T V+, W4+ = T^H V+, W3+ = T^H W1+  (3r products with M per update)
     note_launch(); lane_cols_kernel<<<(nu * r + 127) / 128, 128, 0, s>>>(R.slot_lanes, R.kk, nu, r, KM, R.ucols);
     const int k1 = kp_begin(h, s);
-    trmv_hp(h, R.fp32, 0, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s);
-    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s);
-    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s);
+    trmv_hp(h, R.fp32, 0, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s, R.xh, R.xl);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s, R.xh, R.xl);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s, R.xh, R.xl);
     kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 3 * tri_flops(n, nu * r),
            3 * tri_bytes(n, nu * r, 16, 16, 2), s);
     h->stats.mv_M += 3 * (int64_t)nu * r;
@@ -579,11 +584,12 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     cudaMemsetAsync(R.Lf, 0, sizeof(double2) * (size_t)R.L * R.KM * R.KM, s);
     cudaMemsetAsync(R.p, 0, sizeof(int) * R.L, s);
     // traversal and lane segments
-    const std::vector<int> ord = batch_zigzag(npts, o->grid_nx, o->grid_ny, R.b);
+    const int tb = std::max(1, o->batch_b);  // column-batch size of the traversal
+    const std::vector<int> ord = batch_zigzag(npts, o->grid_nx, o->grid_ny, tb);
     std::vector<int64_t> seg(R.L + 1);
     {
-        const int64_t nbat = (npts + R.b - 1) / R.b;
-        for (int l = 0; l <= R.L; ++l) seg[l] = std::min<int64_t>(npts, (nbat * l / R.L) * R.b);
+        const int64_t nbat = (npts + tb - 1) / tb;
+        for (int l = 0; l <= R.L; ++l) seg[l] = std::min<int64_t>(npts, (nbat * l / R.L) * tb);
     }
     std::vector<int64_t> pos(seg.begin(), seg.end() - 1);
     std::vector<int> started(R.L, 0);
@@ -664,7 +670,8 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         cudaMemcpyAsync(R.items, items_h.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s);
         note_launch(); x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 0);
         launch_normalize(R.U, n, nr, nullptr, s);
-        if ((e = polish_and_rq(h, R, nr, R.fp32 ? 1 : 0, o->max_ir, s)) != cudaSuccess) return cuda_err(e, "polish");
+        if ((e = polish_and_rq(h, R, nr, R.fp32 ? 1 : 0, o->max_ir, items_h, s)) != cudaSuccess)
+            return cuda_err(e, "polish");
         if (R.fp32) { note_launch(); x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 1); }
         note_launch(); refined_values_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.xi, R.s2, R.rr, R.zr, h->norm2,
                                                                R.fp32 ? 1 : 0, R.sig_r, R.res_r);

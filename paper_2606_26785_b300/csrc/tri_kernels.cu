@@ -125,26 +125,33 @@ trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
             if (row < n) {
                 const int64_t dp = lower ? (int64_t)(P * 32 + (li >> 1)) : (int64_t)(li >> 1);
                 const C t = pan[dp * (2 * PH) + 2 * li + (li & 1)];
-                double2 dd = make_double2((double)t.x - s_z[c].x, (double)t.y - s_z[c].y);
-                dd = crecip(dd);
-                d = mk<real>((real)dd.x, (real)dd.y);
+                // 1/(t_ii - z) in the kernel's own precision (a scaled complex
+                // reciprocal: no FP64 instruction in the FP32 solve)
+                d = crecip(mk<real>(t.x - (real)s_z[c].x, t.y - (real)s_z[c].y));
             }
             s_dinv[li * R + c] = d;
         }
         __syncthreads();
 
-        if (warp == 0) {
-            C tot[2][R];
+        // diagonal block: warp w solves columns [w*CPW, w*CPW + CPW) of the
+        // CTA's R right-hand sides (every warp busy when R >= NW)
+        constexpr int CPW = (R + NW - 1) / NW;
+        const int c0 = warp * CPW;
+        if (c0 < R) {
+            C tot[2][CPW];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int row = P * PH + lane + 32 * q;
 #pragma unroll
-                for (int c = 0; c < R; ++c) {
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int c = c0 + cc;
                     C bv = mk<real>(0, 0);
-                    if (row < n && s_col[c] >= 0) bv = X[(int64_t)row * ldx + s_col[c]];
+                    if (c < R) {
+                        if (row < n && s_col[c] >= 0) bv = X[(int64_t)row * ldx + s_col[c]];
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) bv = csub(bv, red[((w * PH) + lane + 32 * q) * R + c]);
-                    tot[q][c] = bv;
+                        for (int w = 0; w < NW; ++w) bv = csub(bv, red[((w * PH) + lane + 32 * q) * R + c]);
+                    }
+                    tot[q][cc] = bv;
                 }
             }
             if (!lower) {
@@ -155,14 +162,15 @@ trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
                         const C *dcol = pan + (int64_t)(i >> 1) * (2 * PH) + (i & 1);
                         const C t0 = dcol[2 * lane], t1 = dcol[2 * (lane + 32)];
 #pragma unroll
-                        for (int c = 0; c < R; ++c) {
-                            C xi = shfl_c(cmul(tot[q][c], s_dinv[i * R + c]), l);
-                            if (lane == l) tot[q][c] = xi;
+                        for (int cc = 0; cc < CPW; ++cc) {
+                            const int c = min(c0 + cc, R - 1);
+                            C xi = shfl_c(cmul(tot[q][cc], s_dinv[i * R + c]), l);
+                            if (lane == l) tot[q][cc] = xi;
                             if (q == 1) {
-                                cfms(tot[0][c], t0, xi);
-                                if (lane < l) cfms(tot[1][c], t1, xi);
+                                cfms(tot[0][cc], t0, xi);
+                                if (lane < l) cfms(tot[1][cc], t1, xi);
                             } else {
-                                if (lane < l) cfms(tot[0][c], t0, xi);
+                                if (lane < l) cfms(tot[0][cc], t0, xi);
                             }
                         }
                     }
@@ -175,14 +183,15 @@ trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
                         const C *dcol = pan + (int64_t)(P * 32 + (i >> 1)) * (2 * PH) + (i & 1);
                         const C t0 = dcol[2 * lane], t1 = dcol[2 * (lane + 32)];
 #pragma unroll
-                        for (int c = 0; c < R; ++c) {
-                            C xi = shfl_c(cmul(tot[q][c], s_dinv[i * R + c]), l);
-                            if (lane == l) tot[q][c] = xi;
+                        for (int cc = 0; cc < CPW; ++cc) {
+                            const int c = min(c0 + cc, R - 1);
+                            C xi = shfl_c(cmul(tot[q][cc], s_dinv[i * R + c]), l);
+                            if (lane == l) tot[q][cc] = xi;
                             if (q == 0) {
-                                if (lane > l) cfms(tot[0][c], t0, xi);
-                                cfms(tot[1][c], t1, xi);
+                                if (lane > l) cfms(tot[0][cc], t0, xi);
+                                cfms(tot[1][cc], t1, xi);
                             } else {
-                                if (lane > l) cfms(tot[1][c], t1, xi);
+                                if (lane > l) cfms(tot[1][cc], t1, xi);
                             }
                         }
                     }
@@ -192,8 +201,10 @@ trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
             for (int q = 0; q < 2; ++q) {
                 const int row = P * PH + lane + 32 * q;
 #pragma unroll
-                for (int c = 0; c < R; ++c) {
-                    const C v = row < n ? tot[q][c] : mk<real>(0, 0);
+                for (int cc = 0; cc < CPW; ++cc) {
+                    const int c = c0 + cc;
+                    if (c >= R) continue;
+                    const C v = row < n ? tot[q][cc] : mk<real>(0, 0);
                     xs[(int64_t)row * R + c] = v;
                     if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
                 }
@@ -223,7 +234,7 @@ static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower
 }
 
 // Column-group width of the solves: FP64 8 columns, FP32 16 columns per CTA.
-constexpr int R64 = 8, R32 = 16, NW_SOLVE = 8;
+constexpr int R64 = 8, R32 = 8, NW_SOLVE = 8;
 int trsv_group_width(int fp32) { return fp32 ? R32 : R64; }
 
 size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols) {
@@ -352,8 +363,9 @@ template <int R, int NW>
 __global__ void __launch_bounds__(NW * 32)
 trmv_ds_kernel(const float2 *__restrict__ Ph, const float2 *__restrict__ Pl, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols,
-               const double2 *__restrict__ X, int64_t ldx, const double2 *__restrict__ B, int64_t ldb,
-               double2 *__restrict__ Y, int64_t ldy, int subtract) {
+               const double2 *__restrict__ X, const float2 *__restrict__ Xh, const float2 *__restrict__ Xl,
+               int64_t ldx, const double2 *__restrict__ B, int64_t ldb, double2 *__restrict__ Y, int64_t ldy,
+               int subtract) {
     __shared__ double2 red[NW][PH][R];
     __shared__ int s_col[R];
     __shared__ double2 s_z[R];
@@ -392,10 +404,17 @@ trmv_ds_kernel(const float2 *__restrict__ Ph, const float2 *__restrict__ Pl, int
             const int cc = s_col[c];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                double2 xv = make_double2(0.0, 0.0);
-                if (cc >= 0 && k0 + u < n) xv = X[(int64_t)(k0 + u) * ldx + cc];
-                const float xrh = (float)xv.x, xih = (float)xv.y;
-                const float xrl = (float)(xv.x - (double)xrh), xil = (float)(xv.y - (double)xih);
+                float xrh = 0.f, xih = 0.f, xrl = 0.f, xil = 0.f;
+                if (cc >= 0 && k0 + u < n) {
+                    if (Xh) {  // pre-split operand: no FP64 instruction in the loop
+                        const float2 vh = Xh[(int64_t)(k0 + u) * ldx + cc], vl = Xl[(int64_t)(k0 + u) * ldx + cc];
+                        xrh = vh.x; xih = vh.y; xrl = vl.x; xil = vl.y;
+                    } else {
+                        const double2 xv = X[(int64_t)(k0 + u) * ldx + cc];
+                        xrh = (float)xv.x; xih = (float)xv.y;
+                        xrl = (float)(xv.x - (double)xrh); xil = (float)(xv.y - (double)xih);
+                    }
+                }
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const float2 h = th[q][u], l = tl[q][u];
@@ -433,14 +452,35 @@ trmv_ds_kernel(const float2 *__restrict__ Ph, const float2 *__restrict__ Pl, int
     }
 }
 
+// x = hi + lo as FP32 pairs for the listed columns (all if cols == nullptr):
+// the only FP64 work of a double-single product, done once per element
+// instead of once per row panel.
+__global__ void split_ds_kernel(const double2 *__restrict__ X, int n, int64_t ldx, const int *__restrict__ cols,
+                                int ncols, float2 *__restrict__ Xh, float2 *__restrict__ Xl) {
+    const int t = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (t >= ncols) return;
+    const int c = cols ? cols[t] : t;
+    for (int i = threadIdx.x >> 5; i < n; i += blockDim.x >> 5) {
+        const double2 v = X[(int64_t)i * ldx + c];
+        const float hx = (float)v.x, hy = (float)v.y;
+        Xh[(int64_t)i * ldx + c] = make_float2(hx, hy);
+        Xl[(int64_t)i * ldx + c] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    }
+}
+
 constexpr int RDS = 4, NW_DS = 8;
 cudaError_t launch_trmv_ds(const float2 *Ph, const float2 *Pl, int n, int n_pad, int lower, const int *cols,
                            const double2 *zc, int ncols, const double2 *X, int64_t ldx, const double2 *B, int64_t ldb,
-                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s) {
+                           double2 *Y, int64_t ldy, int subtract, cudaStream_t s, float2 *Xh, float2 *Xl) {
     if (ncols <= 0) return cudaSuccess;
+    if (Xh && Xl) {
+        note_launch(); split_ds_kernel<<<(ncols + 31) / 32, 256, 0, s>>>(X, n, ldx, cols, ncols, Xh, Xl);
+    } else {
+        Xh = Xl = nullptr;
+    }
     dim3 grid(n_pad / PH, (ncols + RDS - 1) / RDS);
-    note_launch(); trmv_ds_kernel<RDS, NW_DS><<<grid, NW_DS * 32, 0, s>>>(Ph, Pl, n, n_pad, lower, cols, zc, ncols, X, ldx, B, ldb, Y,
-                                                            ldy, subtract);
+    note_launch(); trmv_ds_kernel<RDS, NW_DS><<<grid, NW_DS * 32, 0, s>>>(Ph, Pl, n, n_pad, lower, cols, zc, ncols, X, Xh, Xl, ldx,
+                                                                          B, ldb, Y, ldy, subtract);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,62 @@
+"""Full-size parity on the dense complex Gaussian workload (n = 2000, seed 2,
+200 x 200 grid over [-1.5, 1.5]^2) in the launch configuration bench.py
+times, against stored oracle values at 32 sampled grid points
+(tests/golden/gaussian2000_samples.json, written by the oracle alone), plus
+the strongly nonnormal triangular workload (n = 8000, seed 3) where the mixed
+path is compared with the FP64 path at every point of a coarse sub-grid."""
+import json
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2606_26785_b300 import workloads
+from tests.parity import check_sigma
+
+pytestmark = pytest.mark.gpu
+GOLD = Path(__file__).resolve().parent / "golden"
+
+
+@pytest.fixture(scope="module")
+def gauss():
+    W = workloads.make("gaussian")
+    g = json.loads((GOLD / "gaussian2000_samples.json").read_text())
+    return W, g
+
+
+@pytest.mark.parametrize("mode,precision,rtol", [("invlanc", 1, 1e-8), ("recycle", 1, 1e-8), ("invlanc", 0, 1e-10)])
+def test_gaussian2000_full_grid(gauss, mode, precision, rtol):
+    import paper_2606_26785_b300 as p
+
+    W, g = gauss
+    h = p.Pseudo(W.T)
+    if mode == "invlanc":
+        z = W.z if precision == 1 else W.z[np.array(g["index"])]
+        out = h.grid(z, workloads.EPS_LEVELS, mode=p.INVLANC, precision=precision, rtol=rtol)
+        sig = out["sigma"].cpu().numpy()
+        if precision == 1:
+            sig = sig[np.array(g["index"])]
+    else:
+        out = h.grid(W.z, workloads.EPS_LEVELS, mode=p.RECYCLE, precision=precision, rtol=rtol, r=4, p_max=4,
+                     grid_nx=W.nx, grid_ny=W.ny, batch_b=20)
+        sig = out["sigma"].cpu().numpy()[np.array(g["index"])]
+    rep = check_sigma(sig, np.array(g["sigma_ref"]), n=W.n, fro=g["fro_norm"], schur_err=W.schur_err,
+                      oracle_off=np.array(g["oracle_off"]), rtol=rtol)
+    print(mode, precision, rep, h.stats())
+    assert rep["n_bad"] == 0, rep
+    h.close()
+
+
+def test_triangular8000_mixed_matches_fp64():
+    import paper_2606_26785_b300 as p
+
+    T = workloads.triangular(8000, 3)
+    z = workloads.grid(-1.5, 1.5, -1.5, 1.5, 300, 300)[:: 353]  # 255 points spread over the grid
+    h = p.Pseudo(T)
+    a = h.grid(z, (), mode=p.INVLANC, precision=p.FP64, rtol=1e-10)["sigma"].cpu().numpy()
+    b = h.grid(z, (), mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)["sigma"].cpu().numpy()
+    fro = float(np.linalg.norm(T))
+    ok = a >= 1e-8 * fro
+    err = np.abs(a - b)
+    assert np.all(err[ok] <= 1e-8 * a[ok] + 4 * 8000 * 2.2e-16 * fro), float((err[ok] / a[ok]).max())
+    h.close()
