@@ -207,6 +207,27 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
                   const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision, void *stream);
 
+/* pseudo_solve_noalloc: the FP64 form of pseudo_solve without a workspace, for
+ * callers that cannot allocate device memory (a process that reserved its whole
+ * device-memory budget at start-up, or a latency-critical loop that must not
+ * call cudaMalloc/cudaFree because they can synchronise the device).  The paper
+ * has no counterpart: it is a library-usage entry point.
+ *   X, z, ncols, adjoint, stream : as for pseudo_solve (X device, in place; z device).
+ * Scratch: a fixed 16 MiB array inside the library (2^20 complex doubles), held
+ * by every GPU that loads the library until the process exits.  The solve needs
+ * ceil(ncols / 8) * n_pad * 8 of its elements (n_pad = n rounded up to 64), so
+ * n = 2000 allows up to 512 columns per call; larger calls return
+ * PSEUDO_ERR_ARG with a message and launch nothing.
+ * The first call on a device looks up the array's device address (with the
+ * handle's device current, which the call requires); make that first call
+ * before any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and corrupt each
+ * other's results, so serialise them.  The array keeps the last call's
+ * contents; the solve writes every scratch row before reading it, so nothing
+ * has to be cleared.  No device memory is allocated or freed. */
+int pseudo_solve_noalloc(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
+                         void *stream);
+
 
 #ifdef __cplusplus
 }
