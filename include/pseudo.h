@@ -58,6 +58,8 @@ enum {
 
 enum { PSEUDO_INVLANC = 0, PSEUDO_RECYCLE = 1 };
 enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
+/* pseudo_solve only: the FP32 solve on the CUDA cores instead of the tensor cores */
+enum { PSEUDO_MIXED_CUDACORE = 2 };
 
 /* per-point flags (flags_out) */
 enum {
@@ -94,7 +96,9 @@ typedef struct {
     int io_host;        /* 1: z/sigma/res/flags/member pointers of pseudo_grid are host memory */
     uint64_t seed;      /* seed of the random start vectors */
     int profile;        /* 1: time every hot-kernel launch with CUDA events (pseudo_kernel_stats) */
-    int reserved;
+    int fp32_solver;    /* mixed precision: the FP32 triangular solves run on 0 = the tensor
+                           cores (tcgen05, operands split hi + lo into TF32, 3 products),
+                           1 = the CUDA cores (FP32 FMA) */
 } pseudo_opts;
 
 typedef struct {
@@ -108,6 +112,7 @@ typedef struct {
     int64_t n_updates;   /* updateRecy calls */
     int64_t lanczos_steps;
     int64_t lobpcg_iters;
+    int64_t n_fallback;  /* mixed precision: points redone in FP64 (PSEUDO_PT_IR_FALLBACK) */
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
 } pseudo_stats_t;
 
@@ -166,6 +171,36 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
                 int neps, const pseudo_opts *o, double *sigma_out, double *res_out,
                 int32_t *flags_out, uint32_t *member_out, void *workspace,
                 size_t workspace_bytes, void *stream);
+
+/* Many independent problems in one call (a batch of matrices of uneven size,
+ * each with its own grid): the same result as pseudo_grid on every (hs[m],
+ * z[m], npts[m]) in turn, but the matrices run concurrently on the device so
+ * that small ones, which cannot fill the GPU alone, fill it together.
+ *   hs          : nmat distinct handles (host array).
+ *   z, sigma_out, res_out, flags_out, member_out : host arrays of nmat
+ *                 pointers, each as in pseudo_grid (res/flags/member arrays
+ *                 and their entries may be NULL).
+ *   npts        : host array of nmat point counts (0 allowed).
+ *   eps_levels, neps, o : shared by all matrices, as in pseudo_grid.
+ *   workspace   : device memory of >= pseudo_grid_batch_workspace_bytes(...).
+ * Work is ordered after prior work on `stream`; later work on `stream` waits
+ * for all of it.  Returns the largest non-negative status over the matrices,
+ * or the first error (the message names the matrix). */
+int pseudo_grid_batch_workspace_bytes(const pseudo_handle *hs, int nmat, const int64_t *npts,
+                                      const pseudo_opts *o, size_t *bytes);
+int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo_c64 *const *z, const int64_t *npts,
+                      const double *eps_levels, int neps, const pseudo_opts *o, double *const *sigma_out,
+                      double *const *res_out, int32_t *const *flags_out, uint32_t *const *member_out,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* Recycle mode: where the lanes' recycled subspaces (Alg. 2 state) sit in the
+ * workspace after pseudo_grid returns, for inspection.  out[11] = {lanes, k_max,
+ * row stride of V and W (complex elements), byte offsets of V, W1 = T V,
+ * W3 = T^H T V, W4 = T^H V (n x lanes*k_max row-major, lane l in columns
+ * [l k_max, l k_max + k_max)), H1 = W1^H W1, H2 = W1^H V, L (k_max x k_max per
+ * lane, row-major) and p (int per lane, blocks in use; k = p r columns valid)}.
+ * Errors: ARG. */
+int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t npts, int64_t *out);
 
 /* Counters and phase timings accumulated since create or the last reset. */
 int pseudo_stats(pseudo_handle h, pseudo_stats_t *out);

@@ -11,9 +11,9 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import FP64, INVLANC, MIXED, RECYCLE, Opts, PseudoError, Stats, check  # noqa: F401
+from ._abi import FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, Opts, PseudoError, Stats, check  # noqa: F401
 
-__all__ = ["Pseudo", "default_opts", "FP64", "MIXED", "INVLANC", "RECYCLE", "PseudoError"]
+__all__ = ["Pseudo", "grid_batch", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE", "INVLANC", "RECYCLE", "PseudoError"]
 
 
 def default_opts(**kw) -> Opts:
@@ -147,6 +147,35 @@ class Pseudo:
         out["status"] = rc
         return out
 
+    def recycle_state(self, npts: int, opts: Opts, workspace):
+        """After a recycle-mode grid() call with this workspace: the lanes'
+        recycled subspaces as numpy arrays, one dict per lane with V, W1, W3,
+        W4 (n x k), H1, H2, L (k x k) and p."""
+        torch = _torch()
+        out = (ctypes.c_int64 * 11)()
+        check(self._lib.pseudo_recycle_state_layout(self._h, ctypes.byref(opts), int(npts), out))
+        lanes, km, ld = out[0], out[1], out[2]
+        ws = workspace.cpu().numpy()
+        n = self.n
+
+        def mat(off, rows, cols, ldm):
+            a = ws[off:off + rows * ldm * 16].view(np.complex128).reshape(rows, ldm)
+            return a[:, :cols]
+
+        p_all = ws[out[10]:out[10] + 4 * lanes].view(np.int32)
+        res = []
+        for l in range(lanes):
+            k = int(p_all[l]) * opts.r
+            d = {"p": int(p_all[l])}
+            for name, oi in (("V", 3), ("W1", 4), ("W3", 5), ("W4", 6)):
+                d[name] = mat(out[oi], n, ld, ld)[:, l * km:l * km + k].copy()
+            for name, oi in (("H1", 7), ("H2", 8), ("L", 9)):
+                base = out[oi] + l * km * km * 16
+                d[name] = ws[base:base + km * km * 16].view(np.complex128).reshape(km, km)[:k, :k].copy()
+            res.append(d)
+        del torch
+        return res
+
     def solve(self, X, z, adjoint: bool = False, precision: int = FP64, stream=None):
         """In-place multi-shift triangular solve on a row-major (n, ncols)
         complex128 CUDA tensor X, column c shifted by z[c]."""
@@ -171,3 +200,42 @@ class Pseudo:
         check(self._lib.pseudo_matvec(self._h, _ptr(X), _ptr(B), _ptr(Y), _ptr(zt), ncols, int(adjoint),
                                       int(B is not None), int(precision), _stream_ptr(stream)))
         return Y
+
+
+def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, **kw):
+    """sigma_min for many matrices at once: handles[m] (distinct Pseudo
+    objects) on the complex128 grid zs[m].  The matrices run concurrently on
+    the device.  Returns (list of per-matrix dicts as Pseudo.grid, status)."""
+    torch = _torch()
+    lib = _abi.load()
+    o = Opts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
+    o.io_host = 0  # the binding hands the library device tensors
+    nmat = len(handles)
+    if nmat != len(zs) or nmat < 1:
+        raise ValueError("need one grid per handle")
+    zt = [(z if torch.is_tensor(z) else torch.as_tensor(np.asarray(z, dtype=np.complex128)))
+          .to(device="cuda", dtype=torch.complex128).contiguous() for z in zs]
+    outs = []
+    for z in zt:
+        k = z.numel()
+        outs.append({"sigma": torch.empty(k, dtype=torch.float64, device="cuda"),
+                     "res": torch.empty(k, dtype=torch.float64, device="cuda"),
+                     "flags": torch.empty(k, dtype=torch.int32, device="cuda"),
+                     "member": torch.zeros(k, dtype=torch.int32, device="cuda")})
+    hs = (ctypes.c_void_p * nmat)(*[h._h.value for h in handles])
+    npts = (ctypes.c_int64 * nmat)(*[z.numel() for z in zt])
+
+    def ptrs(key):
+        return (ctypes.c_void_p * nmat)(*[o_[key].data_ptr() for o_ in outs])
+
+    zp = (ctypes.c_void_p * nmat)(*[z.data_ptr() for z in zt])
+    eps = np.ascontiguousarray(np.asarray(eps_levels, dtype=np.float64))
+    need = ctypes.c_size_t()
+    check(lib.pseudo_grid_batch_workspace_bytes(hs, nmat, npts, ctypes.byref(o), ctypes.byref(need)))
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    rc = check(lib.pseudo_grid_batch(
+        hs, nmat, zp, npts, eps.ctypes.data_as(ctypes.c_void_p) if eps.size else None, int(eps.size),
+        ctypes.byref(o), ptrs("sigma"), ptrs("res"), ptrs("flags"), ptrs("member"), _ptr(workspace),
+        workspace.numel(), _stream_ptr(stream)))
+    return outs, rc

@@ -10,13 +10,14 @@ OK = 0
 WARN_NOT_CONVERGED = 1
 ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 INVLANC, RECYCLE = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, MIXED_CUDACORE = 0, 1, 2
 PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4, 8, 16
 
 EXPORTED = (
     "pseudo_opts_default", "pseudo_create", "pseudo_workspace_bytes", "pseudo_grid", "pseudo_stats",
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
-    "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count",
+    "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count", "pseudo_recycle_state_layout",
+    "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch",
 )
 
 
@@ -27,7 +28,7 @@ class Opts(ctypes.Structure):
         ("shift_batch", ctypes.c_int), ("eps_shift_rel", ctypes.c_double), ("tau", ctypes.c_double),
         ("omega", ctypes.c_double), ("eta", ctypes.c_double), ("rtol", ctypes.c_double),
         ("maxiter_lanczos", ctypes.c_int), ("maxiter_lobpcg", ctypes.c_int), ("max_ir", ctypes.c_int),
-        ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("fp32_solver", ctypes.c_int),
     ]
 
 
@@ -42,7 +43,7 @@ KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos")
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "sv_R", "mv_M", "mv_M_fp64_refine", "n_points", "n_accepted", "n_refined", "n_not_converged",
-        "n_updates", "lanczos_steps", "lobpcg_iters")] + [(k, ctypes.c_double) for k in (
+        "n_updates", "lanczos_steps", "lobpcg_iters", "n_fallback")] + [(k, ctypes.c_double) for k in (
         "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")]
 
     def as_dict(self):
@@ -82,10 +83,13 @@ def load(build_if_missing: bool = True):
     lib.pseudo_last_error.restype = ctypes.c_char_p
     lib.pseudo_solve_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_solve.argtypes = [vp, vp, vp, i64, ci, ci, vp, ctypes.c_size_t, vp]
+    lib.pseudo_recycle_state_layout.argtypes = [vp, po, i64, ctypes.POINTER(i64)]
     lib.pseudo_launch_count.argtypes = []
     lib.pseudo_launch_count.restype = ctypes.c_int64
     lib.pseudo_kernel_stats.argtypes = [vp, ci, ctypes.POINTER(KStat)]
     lib.pseudo_matvec.argtypes = [vp, vp, vp, vp, vp, i64, ci, ci, ci, vp]
+    lib.pseudo_grid_batch_workspace_bytes.argtypes = [vp, ci, vp, po, ctypes.POINTER(ctypes.c_size_t)]
+    lib.pseudo_grid_batch.argtypes = [vp, ci, vp, vp, vp, ci, po, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:
         fn = getattr(lib, name)
         if name not in ("pseudo_destroy", "pseudo_last_error", "pseudo_launch_count"):

@@ -55,6 +55,12 @@ struct pseudo_ctx {
     float2 *U32 = nullptr, *L32 = nullptr;   // the same in FP32 (the high parts)
     float2 *U32lo = nullptr, *L32lo = nullptr;  // fl32(T - fl32(T)): low parts for double-single products
     double2 *diag = nullptr;                 // T_ii (the eigenvalues of C)
+    // tensor-core solve: A'' chunks (TF32 hi/lo, shared-memory image) and
+    // FP32 diagonal blocks of T and T^H; device error word of bounded waits
+    float *tcA_U = nullptr, *tcA_L = nullptr;
+    float2 *tcD_U = nullptr, *tcD_L = nullptr;
+    int *dev_err = nullptr;
+    int fp32_solver = 0;                     // 0 tensor cores, 1 CUDA cores
     double norm_fro = 0.0, norm2 = 0.0;      // ||T||_F and a 2-norm estimate
     pseudo_stats_t stats;
 };
@@ -98,6 +104,7 @@ void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c,
 int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
 void recycle_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *plan);
 int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
+void recycle_state_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, int64_t *out);
 void launch_convert_64_to_32(const double2 *a, float2 *b, int64_t cnt, cudaStream_t s);
 void launch_convert_32_to_64(const float2 *a, double2 *b, int64_t cnt, cudaStream_t s);
 }  // namespace pseudo

@@ -29,6 +29,24 @@ cudaError_t launch_extract_diag(const double2 *U, int n, int n_pad, double2 *d, 
 
 }  // namespace pseudo
 
+struct pseudo_ctx;
+namespace pseudo {
+// trsv_tc.cu: the tensor-core solve (row panels of 128; n_pad is a multiple of 128)
+constexpr int TC_MB = 128;
+int64_t tc_pack_floats(int n_pad);
+int64_t tc_diag_elems(int n_pad);
+void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, float *AL, float2 *DU, float2 *DL,
+                    cudaStream_t s);
+cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                           const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
+// The FP32 multi-shift solve of the handle's choice (tensor cores or CUDA
+// cores); xs is trsv_scratch_bytes(1, n_pad, ncols) of scratch.
+cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                    const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
+// unit roundoff of the FP32 solve in use (for the refinement plan)
+double solve32_unit_roundoff(const pseudo_ctx *h);
+}  // namespace pseudo
+
 namespace pseudo {
 // lanczos.cu
 constexpr int LANCZOS_MMAX = 64;
@@ -124,5 +142,16 @@ void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, cons
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
-                        cudaStream_t s);
+                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s);
+void launch_fb_gather(const int *list, int cnt, const double2 *zall, double2 *zc, cudaStream_t s);
+void launch_fb_scatter(const int *list, int cnt, const double *sc, const double *rc, const int32_t *fc,
+                       const uint32_t *mc, double *sigma, double *res, int32_t *flags, uint32_t *member,
+                       cudaStream_t s);
+}  // namespace pseudo
+
+namespace pseudo {
+template <typename real>
+void launch_slot_orth_grid(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, int mmax,
+                           const int *active, double *alpha, double *beta, int passes, double2 *Hp, double *nrm2,
+                           double *alpha_acc, cudaStream_t s);
 }  // namespace pseudo

@@ -28,6 +28,8 @@ struct LancLayout {
     bool fp32 = false;
     void *Q = nullptr, *W = nullptr, *xs = nullptr;
     double *alpha = nullptr, *beta = nullptr, *svec = nullptr, *theta = nullptr;
+    double2 *Hp = nullptr;                           // Gram-Schmidt coefficients, S x (mmax+1)
+    double *nrm2 = nullptr, *alpha_acc = nullptr;   // per-slot partial sums
     int *jv = nullptr, *active = nullptr, *cols = nullptr, *cnt = nullptr, *convd = nullptr, *pt = nullptr;
     int *counters = nullptr, *nbad = nullptr;
     double2 *zslot = nullptr, *startv = nullptr;
@@ -41,7 +43,18 @@ struct LancLayout {
     double *sig_dev = nullptr, *res_dev = nullptr;
     int32_t *flags_dev = nullptr;
     uint32_t *member_dev = nullptr;
+    // mixed precision: points redone in FP64 (list, count) and the compact
+    // per-chunk arrays of that pass (capacity CH)
+    int *fb_list = nullptr, *fb_cnt = nullptr;
+    int CH = 0;
+    double2 *fb_z = nullptr;
+    double *fb_sig = nullptr, *fb_res = nullptr;
+    int32_t *fb_flags = nullptr;
+    uint32_t *fb_member = nullptr;
 };
+
+// Slots of the FP64 pass that mixed precision hands its hard points to.
+constexpr int FB_SLOTS = 256;
 
 static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool fp32, int mmax) {
     int64_t S = o->shift_batch > 0 ? o->shift_batch : 8192;
@@ -55,10 +68,11 @@ static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool 
     return (int)std::max<int64_t>(S, 1);
 }
 
-static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, LancLayout &L, bool on_host) {
-    L.fp32 = o->precision == PSEUDO_MIXED;
+static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, LancLayout &L, bool on_host,
+                        bool fp32, int slots = 0) {
+    L.fp32 = fp32;
     L.mmax = o->maxiter_lanczos;
-    L.S = choose_slots(h, o, npts, L.fp32, L.mmax);
+    L.S = slots > 0 ? (int)std::min<int64_t>(slots, npts) : choose_slots(h, o, npts, L.fp32, L.mmax);
     L.F = 2 * L.S;
     const size_t n = h->n, S = L.S, F = L.F, esz = L.fp32 ? sizeof(float2) : sizeof(double2);
     L.Q = c.take((size_t)(L.mmax + 1) * n * S * esz);
@@ -68,6 +82,9 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     L.beta = c.get<double>(S * L.mmax);
     L.svec = c.get<double>(S * L.mmax);
     L.theta = c.get<double>(S);
+    L.Hp = c.get<double2>(S * (L.mmax + 1));
+    L.nrm2 = c.get<double>(S);
+    L.alpha_acc = c.get<double>(S);
     L.jv = c.get<int>(S);
     L.active = c.get<int>(S);
     L.cols = c.get<int>(S);
@@ -100,6 +117,14 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
         L.xl = c.get<float2>(n * F);
         L.need = c.get<int>(F);
         L.perm = c.get<int>(F);
+        L.fb_list = c.get<int>(npts);
+        L.fb_cnt = c.get<int>(4);
+        L.CH = 4 * FB_SLOTS;
+        L.fb_z = c.get<double2>(L.CH);
+        L.fb_sig = c.get<double>(L.CH);
+        L.fb_res = c.get<double>(L.CH);
+        L.fb_flags = c.get<int32_t>(L.CH);
+        L.fb_member = c.get<uint32_t>(L.CH);
     }
     if (on_host) {
         L.z_dev = c.get<double2>(npts);
@@ -111,13 +136,15 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
 }
 
 void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *) {
-    LancLayout L;
-    lanc_layout(h, o, npts, c, L, o->io_host != 0);
+    LancLayout L, Lfb;
+    const bool mixed = o->precision == PSEUDO_MIXED;
+    lanc_layout(h, o, npts, c, L, o->io_host != 0, mixed);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
 }
 
 // Refine (mixed) and finalise the P finished points held in columns [0, P)
 // of the finished buffer.
-static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int P, const GridIO &io, double *sig_all,
+static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int P, int neps, double *sig_all,
                         double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s) {
     const int n = h->n, F = L.F;
     cudaError_t e;
@@ -152,39 +179,23 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     kp_end(h, k0, kc, 2 * tri_flops(n, P), 2 * tri_bytes(n, P, 16, 16, 2), s);
     h->stats.mv_M_fp64_refine += 2 * (int64_t)P;
     launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);
+    // kappa * u above 1/32: the planned refinement contracts by less than 4 per step
     launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0, h->norm2, L.eps,
-                       io.neps, sig_all, res_all, flags_all, member_all, L.nbad, s);
+                       neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), 1.0 / 32.0,
+                       L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;
 }
 
-int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s) {
-    LancLayout L;
-    lanc_layout(h, o, io.npts, c, L, io.on_host);
-    if (c.overflow) return set_err(PSEUDO_ERR_WORKSPACE, "workspace too small");
+// Continuous-batching Lanczos over the npts points zall (device) with the
+// outputs in the same order; eps levels must already be in L.eps.
+static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const double2 *zall, int64_t npts, int neps,
+                      double *sig_all, double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s) {
     const int n = h->n, S = L.S;
-    const int64_t npts = io.npts;
     const int64_t qs = (int64_t)n * S;
     cudaError_t e;
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventRecord(ev0, s);
-
-    const double2 *zall = io.z;
-    double *sig_all = io.sigma, *res_all = io.res;
-    int32_t *flags_all = io.flags;
-    uint32_t *member_all = io.member;
-    if (io.on_host) {
-        cudaMemcpyAsync(L.z_dev, io.z, npts * sizeof(double2), cudaMemcpyHostToDevice, s);
-        zall = L.z_dev;
-        sig_all = L.sig_dev;
-        res_all = io.res ? L.res_dev : nullptr;
-        flags_all = io.flags ? L.flags_dev : nullptr;
-        member_all = io.member ? L.member_dev : nullptr;
-    }
-    if (io.neps > 0) cudaMemcpyAsync(L.eps, io.eps_host, io.neps * sizeof(double), cudaMemcpyHostToDevice, s);
     cudaMemsetAsync(L.nbad, 0, sizeof(int), s);
     cudaMemsetAsync(L.counters, 0, 4 * sizeof(int), s);
+    if (L.fb_cnt) cudaMemsetAsync(L.fb_cnt, 0, sizeof(int), s);
     launch_start_vector(L.startv, n, o->seed, s);
 
     const double rt = o->rtol > 0.0 ? o->rtol : 1e-8;
@@ -213,7 +224,7 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "lanczos");
         const int ncnt = host[0], nfin = host[2];
         if (nfin >= S || (ncnt == 0 && nfin > 0)) {
-            const int rc = finish_batch(h, o, L, nfin, io, sig_all, res_all, flags_all, member_all, s);
+            const int rc = finish_batch(h, o, L, nfin, neps, sig_all, res_all, flags_all, member_all, s);
             if (rc < 0) return rc;
             cudaMemsetAsync(L.counters + 1, 0, sizeof(int), s);
         }
@@ -222,14 +233,15 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             float2 *Q = (float2 *)L.Q, *W = (float2 *)L.W;
             launch_slot_copy<float>(Q, qs, W, n, S, L.jv, L.active, s);
             int k0 = kp_begin(h, s);
-            e = launch_trsv32(h->L32, n, h->n_pad, 1, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
+            e = solve32(h, 1, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
             kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
             k0 = kp_begin(h, s);
             if (e == cudaSuccess)
-                e = launch_trsv32(h->U32, n, h->n_pad, 0, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
+                e = solve32(h, 0, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
             kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
             k0 = kp_begin(h, s);
-            launch_slot_orth<float>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, s);
+            launch_slot_orth_grid<float>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, L.Hp, L.nrm2,
+                                         L.alpha_acc, s);
             kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
         } else {
             double2 *Q = (double2 *)L.Q, *W = (double2 *)L.W;
@@ -242,7 +254,8 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
                 e = launch_trsv64(h->U64, n, h->n_pad, 0, L.cols, L.zslot, ncnt, L.cnt, W, S, (double2 *)L.xs, s);
             kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
             k0 = kp_begin(h, s);
-            launch_slot_orth<double>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, s);
+            launch_slot_orth_grid<double>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, L.Hp, L.nrm2,
+                                          L.alpha_acc, s);
             kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
         }
         if (e != cudaSuccess) return cuda_err(e, "lanczos solve");
@@ -252,14 +265,62 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         harvest();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "lanczos step");
     }
+    return 0;
+}
+
+int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s) {
+    LancLayout L, Lfb;
+    const bool mixed = o->precision == PSEUDO_MIXED;
+    lanc_layout(h, o, io.npts, c, L, io.on_host, mixed);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
+    if (c.overflow) return set_err(PSEUDO_ERR_WORKSPACE, "workspace too small");
+    const int64_t npts = io.npts;
+    cudaError_t e;
+    cudaEvent_t ev0, ev1;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, s);
+
+    const double2 *zall = io.z;
+    double *sig_all = io.sigma, *res_all = io.res;
+    int32_t *flags_all = io.flags;
+    uint32_t *member_all = io.member;
+    if (io.on_host) {
+        cudaMemcpyAsync(L.z_dev, io.z, npts * sizeof(double2), cudaMemcpyHostToDevice, s);
+        zall = L.z_dev;
+        sig_all = L.sig_dev;
+        res_all = io.res ? L.res_dev : nullptr;
+        flags_all = io.flags ? L.flags_dev : nullptr;
+        member_all = io.member ? L.member_dev : nullptr;
+    }
+    if (io.neps > 0) cudaMemcpyAsync(L.eps, io.eps_host, io.neps * sizeof(double), cudaMemcpyHostToDevice, s);
+    int rc = run_points(h, o, L, zall, npts, io.neps, sig_all, res_all, flags_all, member_all, s);
+    if (rc < 0) return rc;
+    int nbad = 0, nfb = 0;
+    cudaMemcpyAsync(&nbad, L.nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (mixed) cudaMemcpyAsync(&nfb, L.fb_cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "pseudo_grid");
+    // the points mixed precision could not vouch for, in FP64, CH at a time
+    for (int off = 0; off < nfb; off += L.CH) {
+        const int cnt = std::min(L.CH, nfb - off);
+        if (io.neps > 0) cudaMemcpyAsync(Lfb.eps, L.eps, io.neps * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        launch_fb_gather(L.fb_list + off, cnt, zall, L.fb_z, s);
+        rc = run_points(h, o, Lfb, L.fb_z, cnt, io.neps, L.fb_sig, L.fb_res, L.fb_flags, L.fb_member, s);
+        if (rc < 0) return rc;
+        launch_fb_scatter(L.fb_list + off, cnt, L.fb_sig, res_all ? L.fb_res : nullptr, L.fb_flags,
+                          L.fb_member, sig_all, res_all, flags_all, member_all, s);
+        int nb = 0;
+        cudaMemcpyAsync(&nb, Lfb.nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback");
+        nbad += nb;
+    }
+    h->stats.n_fallback += nfb;
     if (io.on_host) {
         cudaMemcpyAsync(io.sigma, sig_all, npts * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (io.res) cudaMemcpyAsync(io.res, res_all, npts * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (io.flags) cudaMemcpyAsync(io.flags, flags_all, npts * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (io.member) cudaMemcpyAsync(io.member, member_all, npts * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     }
-    int nbad = 0;
-    cudaMemcpyAsync(&nbad, L.nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaEventRecord(ev1, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "pseudo_grid");
     float ms = 0.f;

@@ -594,15 +594,27 @@ __global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const 
                                    const double *__restrict__ s2, const double *__restrict__ rr, int use_rq,
                                    double norm2, const double *__restrict__ eps, int neps, double *__restrict__ sigma_out,
                                    double *__restrict__ res_out, int32_t *__restrict__ flags_out,
-                                   uint32_t *__restrict__ member_out, int *__restrict__ nbad) {
+                                   uint32_t *__restrict__ member_out, int *__restrict__ nbad, double u_solve,
+                                   double fb_ku, int *__restrict__ fb_list, int *__restrict__ fb_cnt) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P) return;
     const double th = fin_theta[t];
     const double rq = sqrt(fmax(s2[t], 0.0));
-    const double sig = use_rq ? rq : (th > 0.0 ? 1.0 / sqrt(th) : 0.0);
+    const double sl = th > 0.0 ? 1.0 / sqrt(th) : 0.0;
+    const double sig = use_rq ? rq : sl;
     const double2 z = fin_z[t];
     const double mz = norm2 + sqrt(z.x * z.x + z.y * z.y);
     const int g = fin_pt[t];
+    if (fb_list) {
+        // mixed precision cannot be trusted here: the FP32 recurrence did not
+        // converge, or kappa = ||M|| / sigma is so large that the refinement
+        // of the solves stops contracting; such points are redone in FP64
+        const double sg = fmin(sig, sl > 0.0 ? sl : sig);
+        if (!fin_conv[t] || !(sg > 0.0) || (mz / sg) * u_solve > fb_ku) {
+            fb_list[atomicAdd(fb_cnt, 1)] = g;
+            return;
+        }
+    }
     int fl = PSEUDO_PT_REFINED;
     if (!fin_conv[t]) { fl |= PSEUDO_PT_NOT_CONVERGED; atomicAdd(nbad, 1); }
     sigma_out[g] = sig;
@@ -644,11 +656,41 @@ void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, cons
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
-                        cudaStream_t s) {
+                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s) {
     if (P > 0) {
         note_launch(); fin_scatter_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, fin_pt, fin_z, fin_theta, fin_conv, s2, rr, use_rq, norm2,
                                                                         eps, neps, sigma_out, res_out, flags_out,
-                                                                        member_out, nbad);
+                                                                        member_out, nbad, u_solve, fb_ku, fb_list,
+                                                                        fb_cnt);
+    }
+}
+
+__global__ void fb_gather_kernel(const int *__restrict__ list, int cnt, const double2 *__restrict__ zall,
+                                 double2 *__restrict__ zc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) zc[t] = zall[list[t]];
+}
+__global__ void fb_scatter_kernel(const int *__restrict__ list, int cnt, const double *__restrict__ sc,
+                                  const double *__restrict__ rc, const int32_t *__restrict__ fc,
+                                  const uint32_t *__restrict__ mc, double *__restrict__ sigma, double *__restrict__ res,
+                                  int32_t *__restrict__ flags, uint32_t *__restrict__ member) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const int g = list[t];
+    sigma[g] = sc[t];
+    if (res) res[g] = rc[t];
+    if (flags) flags[g] = fc[t] | PSEUDO_PT_IR_FALLBACK;
+    if (member) member[g] = mc[t];
+}
+void launch_fb_gather(const int *list, int cnt, const double2 *zall, double2 *zc, cudaStream_t s) {
+    if (cnt > 0) { note_launch(); fb_gather_kernel<<<(cnt + 127) / 128, 128, 0, s>>>(list, cnt, zall, zc); }
+}
+void launch_fb_scatter(const int *list, int cnt, const double *sc, const double *rc, const int32_t *fc,
+                       const uint32_t *mc, double *sigma, double *res, int32_t *flags, uint32_t *member,
+                       cudaStream_t s) {
+    if (cnt > 0) {
+        note_launch();
+        fb_scatter_kernel<<<(cnt + 127) / 128, 128, 0, s>>>(list, cnt, sc, rc, fc, mc, sigma, res, flags, member);
     }
 }
 template void launch_slot_copy<float>(const float2 *, int64_t, float2 *, int, int, const int *, const int *, cudaStream_t);
@@ -665,4 +707,151 @@ template void launch_slot_harvest<double>(double2 *, int64_t, int, int, int, con
                                           double2 *, int, int *, double2 *, double *, int *, const double2 *,
                                           cudaStream_t);
 
+}  // namespace pseudo
+
+// ============ grid-parallel reorthogonalisation for the slot scheme
+// One classical Gram-Schmidt pass is split into a dot kernel and an update
+// kernel whose CTAs each own 32 columns x a slice of rows, so that the whole
+// GPU streams Q (the pass is bound by reading Q twice).
+namespace pseudo {
+constexpr int OS_ROWS = 128;  // rows per CTA slice
+
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+orth_dots_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, const cx_t<real> *__restrict__ W, int n, int S,
+                 const int *__restrict__ jv, const int *__restrict__ active, int ldh, double2 *__restrict__ Hp) {
+    using C = cx_t<real>;
+    __shared__ double2 red[ORTH_WARPS][TCH][32];
+    __shared__ int s_jmax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool on = (c < S) && active[c] == 1;
+    const int jc = on ? jv[c] : -1;
+    if (threadIdx.x == 0) s_jmax = -1;
+    __syncthreads();
+    if (warp == 0 && on) atomicMax(&s_jmax, jc);
+    __syncthreads();
+    const int jmax = s_jmax;
+    if (jmax < 0) return;
+    const int r0 = blockIdx.y * OS_ROWS, r1 = min(n, r0 + OS_ROWS);
+    const int cc = on ? c : 0;
+    for (int t0 = 0; t0 <= jmax; t0 += TCH) {
+        C acc[TCH];
+#pragma unroll
+        for (int u = 0; u < TCH; ++u) acc[u] = mk<real>(0, 0);
+        if (on && t0 <= jc)
+            for (int i = r0 + warp; i < r1; i += ORTH_WARPS) {
+                const C wv = W[(int64_t)i * S + cc];
+#pragma unroll
+                for (int u = 0; u < TCH; ++u)
+                    if (t0 + u <= jc) cfma(acc[u], cconj(Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc]), wv);
+            }
+#pragma unroll
+        for (int u = 0; u < TCH; ++u) red[warp][u][lane] = make_double2((double)acc[u].x, (double)acc[u].y);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TCH * 32; e += blockDim.x) {
+            const int u = e / 32, l = e % 32, col = blockIdx.x * 32 + l;
+            if (col < S && active[col] == 1 && t0 + u <= jv[col]) {
+                double2 s = make_double2(0.0, 0.0);
+                for (int w = 0; w < ORTH_WARPS; ++w) { s.x += red[w][u][l].x; s.y += red[w][u][l].y; }
+                atomicAdd(&Hp[(int64_t)col * ldh + t0 + u].x, s.x);
+                atomicAdd(&Hp[(int64_t)col * ldh + t0 + u].y, s.y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// w -= sum_t h_t q_t over the slice's rows; partial ||w||^2 into nrm2 (when
+// non-null) and, from the first slice, alpha_acc += Re h_{j}.
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+orth_update_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restrict__ W, int n, int S,
+                   const int *__restrict__ jv, const int *__restrict__ active, int ldh, const double2 *__restrict__ Hp,
+                   double *__restrict__ nrm2, double *__restrict__ alpha_acc) {
+    using C = cx_t<real>;
+    __shared__ double s_n[ORTH_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const bool on = (c < S) && active[c] == 1;
+    const int jc = on ? jv[c] : -1;
+    const int r0 = blockIdx.y * OS_ROWS, r1 = min(n, r0 + OS_ROWS);
+    const int cc = on ? c : 0;
+    real sp = 0;
+    if (on) {
+        if (blockIdx.y == 0 && warp == 0) alpha_acc[c] += Hp[(int64_t)c * ldh + jc].x;
+        for (int t0 = 0; t0 <= jc; t0 += TCH) {
+            C hc[TCH];
+#pragma unroll
+            for (int u = 0; u < TCH; ++u) {
+                const double2 hv = t0 + u <= jc ? Hp[(int64_t)c * ldh + t0 + u] : make_double2(0.0, 0.0);
+                hc[u] = mk<real>((real)hv.x, (real)hv.y);
+            }
+            const bool last = t0 + TCH > jc;
+            for (int i = r0 + warp; i < r1; i += ORTH_WARPS) {
+                C wv = W[(int64_t)i * S + cc];
+#pragma unroll
+                for (int u = 0; u < TCH; ++u)
+                    if (t0 + u <= jc) cfms(wv, Q[(int64_t)(t0 + u) * qs + (int64_t)i * S + cc], hc[u]);
+                W[(int64_t)i * S + cc] = wv;
+                if (last) sp += wv.x * wv.x + wv.y * wv.y;
+            }
+        }
+    }
+    if (!nrm2) return;
+    s_n[warp][lane] = (double)sp;
+    __syncthreads();
+    if (warp == 0 && on) {
+        double t = 0.0;
+        for (int w = 0; w < ORTH_WARPS; ++w) t += s_n[w][lane];
+        atomicAdd(&nrm2[c], t);
+    }
+}
+
+// q_{j+1} = w / ||w||, alpha_j, beta_j
+template <typename real>
+__global__ void __launch_bounds__(ORTH_WARPS * 32)
+orth_finish_kernel(cx_t<real> *__restrict__ Q, int64_t qs, const cx_t<real> *__restrict__ W, int n, int S,
+                   const int *__restrict__ jv, const int *__restrict__ active, const double *__restrict__ nrm2,
+                   const double *__restrict__ alpha_acc, int mmax, double *__restrict__ alpha,
+                   double *__restrict__ beta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    if (c >= S || active[c] != 1) return;
+    const int jc = jv[c];
+    const double b = sqrt(nrm2[c]);
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    const int r0 = blockIdx.y * OS_ROWS, r1 = min(n, r0 + OS_ROWS);
+    for (int i = r0 + warp; i < r1; i += ORTH_WARPS) {
+        const cx_t<real> wv = W[(int64_t)i * S + c];
+        Q[(int64_t)(jc + 1) * qs + (int64_t)i * S + c] = mk<real>((real)(wv.x * inv), (real)(wv.y * inv));
+    }
+    if (blockIdx.y == 0 && warp == 0) {
+        alpha[(int64_t)c * mmax + jc] = alpha_acc[c];
+        beta[(int64_t)c * mmax + jc] = b;
+    }
+}
+
+template <typename real>
+void launch_slot_orth_grid(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, int mmax,
+                           const int *active, double *alpha, double *beta, int passes, double2 *Hp, double *nrm2,
+                           double *alpha_acc, cudaStream_t s) {
+    const dim3 grid((S + 31) / 32, (n + OS_ROWS - 1) / OS_ROWS);
+    const int ldh = mmax + 1;
+    cudaMemsetAsync(alpha_acc, 0, sizeof(double) * S, s);
+    cudaMemsetAsync(nrm2, 0, sizeof(double) * S, s);
+    for (int pass = 0; pass < passes; ++pass) {
+        cudaMemsetAsync(Hp, 0, sizeof(double2) * (size_t)S * ldh, s);
+        note_launch(); orth_dots_kernel<real><<<grid, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, jv, active, ldh, Hp);
+        note_launch(); orth_update_kernel<real><<<grid, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, jv, active, ldh, Hp,
+                                                                                 pass == passes - 1 ? nrm2 : nullptr,
+                                                                                 alpha_acc);
+    }
+    note_launch(); orth_finish_kernel<real><<<grid, ORTH_WARPS * 32, 0, s>>>(Q, qs, W, n, S, jv, active, nrm2, alpha_acc,
+                                                                             mmax, alpha, beta);
+}
+template void launch_slot_orth_grid<float>(float2 *, int64_t, float2 *, int, int, const int *, int, const int *, double *,
+                                           double *, int, double2 *, double *, double *, cudaStream_t);
+template void launch_slot_orth_grid<double>(double2 *, int64_t, double2 *, int, int, const int *, int, const int *,
+                                            double *, double *, int, double2 *, double *, double *, cudaStream_t);
 }  // namespace pseudo

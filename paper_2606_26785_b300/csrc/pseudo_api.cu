@@ -87,7 +87,7 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     cudaStream_t s = (cudaStream_t)stream;
     pseudo_ctx *h = new pseudo_ctx();
     h->n = (int)n;
-    h->n_pad = (int)((n + PH - 1) / PH * PH);
+    h->n_pad = (int)((n + TC_MB - 1) / TC_MB * TC_MB);  // a multiple of both panel heights
     cudaGetDevice(&h->dev);
     const int64_t psz = packed_size(h->n_pad);
     cudaError_t e;
@@ -108,6 +108,12 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaMalloc(&h->U32lo, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc U32lo"));
     if ((e = cudaMalloc(&h->L32lo, psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc L32lo"));
     if ((e = cudaMalloc(&h->diag, n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc diag"));
+    if ((e = cudaMalloc(&h->tcA_U, tc_pack_floats(h->n_pad) * sizeof(float) + 16)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcA_U"));
+    if ((e = cudaMalloc(&h->tcA_L, tc_pack_floats(h->n_pad) * sizeof(float) + 16)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcA_L"));
+    if ((e = cudaMalloc(&h->tcD_U, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_U"));
+    if ((e = cudaMalloc(&h->tcD_L, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_L"));
+    if ((e = cudaMalloc(&h->dev_err, sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc dev_err"));
+    if ((e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), s)) != cudaSuccess) return fail(cuda_err(e, "memset"));
     if ((e = cudaMalloc(&bad, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if ((e = cudaMalloc(&dsum, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if (t_on_host) {
@@ -118,6 +124,7 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
         Td = (double2 *)T;
     }
     launch_pack_panels(Td, ldT, (int)n, h->n_pad, h->U64, h->L64, h->U32, h->L32, s);
+    launch_pack_tc(Td, ldT, (int)n, h->n_pad, h->tcA_U, h->tcA_L, h->tcD_U, h->tcD_L, s);
     launch_pack_lo(h->U64, h->U32, h->U32lo, psz, s);
     launch_pack_lo(h->L64, h->L32, h->L32lo, psz, s);
     cudaMemsetAsync(bad, 0, sizeof(int), s);
@@ -173,6 +180,11 @@ void pseudo_destroy(pseudo_handle h) {
     cudaFree(h->U32lo);
     cudaFree(h->L32lo);
     cudaFree(h->diag);
+    cudaFree(h->tcA_U);
+    cudaFree(h->tcA_L);
+    cudaFree(h->tcD_U);
+    cudaFree(h->tcD_L);
+    cudaFree(h->dev_err);
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     delete h;
 }
@@ -204,6 +216,20 @@ int pseudo_kernel_stats(pseudo_handle h, int kclass, pseudo_kstat *out) {
     return PSEUDO_OK;
 }
 
+// A bounded wait inside a tensor-core kernel that gave up leaves a mark in
+// dev_err (the kernel returned early and its results are invalid).
+static int check_dev_err(pseudo_ctx *h, cudaStream_t s) {
+    int v = 0;
+    cudaMemcpyAsync(&v, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(e, "stream");
+    if (v) {
+        cudaMemsetAsync(h->dev_err, 0, sizeof(int), s);
+        return set_err(PSEUDO_ERR_TIMEOUT, "a tensor-core solve timed out waiting on its pipeline");
+    }
+    return PSEUDO_OK;
+}
+
 int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) {
     if (!h || !bytes || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
     Carver c;
@@ -218,7 +244,8 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
                  void *workspace, size_t workspace_bytes, void *stream) {
     clear_err();
     if (!h || !X || !z || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
-    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED) return set_err(PSEUDO_ERR_ARG, "bad precision");
+    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE)
+        return set_err(PSEUDO_ERR_ARG, "bad precision");
     if (ncols == 0) return PSEUDO_OK;
     size_t need = 0;
     pseudo_solve_workspace_bytes(h, ncols, &need);
@@ -235,11 +262,17 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
         float2 *xs = (float2 *)c.take(trsv_scratch_bytes(1, h->n_pad, ncols));
         float2 *X32 = (float2 *)c.take((size_t)h->n * ncols * sizeof(float2));
         launch_convert_64_to_32((const double2 *)X, X32, (int64_t)h->n * ncols, s);
-        e = launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
-                          nullptr, X32, ncols, xs, s);
+        const int keep = h->fp32_solver;
+        h->fp32_solver = precision == PSEUDO_MIXED ? 0 : 1;
+        e = solve32(h, lower, nullptr, (const double2 *)z, (int)ncols, nullptr, X32, ncols, xs, s);
+        h->fp32_solver = keep;
         launch_convert_32_to_64(X32, (double2 *)X, (int64_t)h->n * ncols, s);
     }
     if (e != cudaSuccess) return cuda_err(e, "pseudo_solve");
+    if (precision == PSEUDO_MIXED) {
+        const int rc = check_dev_err(h, s);
+        if (rc) return rc;
+    }
     h->stats.sv_R += ncols;
     return PSEUDO_OK;
 }
@@ -298,6 +331,16 @@ int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, 
     return PSEUDO_OK;
 }
 
+int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t npts, int64_t *out) {
+    clear_err();
+    if (!h || !o || !out || npts < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (o->mode != PSEUDO_RECYCLE) return set_err(PSEUDO_ERR_ARG, "recycle mode only");
+    const int rc = check_opts(o);
+    if (rc) return rc;
+    recycle_state_layout(h, o, npts, out);
+    return PSEUDO_OK;
+}
+
 int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double *eps_levels, int neps,
                 const pseudo_opts *o, double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out,
                 void *workspace, size_t workspace_bytes, void *stream) {
@@ -335,7 +378,12 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     h->prof = o->profile != 0;
     h->recs.clear();
     h->evn = 0;
-    const int res = o->mode == PSEUDO_INVLANC ? invlanc_run(h, o, io, c, s) : recycle_run(h, o, io, c, s);
+    h->fp32_solver = o->fp32_solver;
+    int res = o->mode == PSEUDO_INVLANC ? invlanc_run(h, o, io, c, s) : recycle_run(h, o, io, c, s);
+    if (res >= 0 && o->precision == PSEUDO_MIXED) {
+        const int rc = check_dev_err(h, s);
+        if (rc) res = rc;
+    }
     if (h->prof) {
         cudaStreamSynchronize(s);
         kp_resolve(h);

@@ -264,6 +264,20 @@ void recycle_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c,
     recy_layout(h, o, npts, c, R, o->io_host != 0);
 }
 
+// Where the lanes' recycle state sits in the workspace after pseudo_grid:
+// out = {lanes, k_max, row stride of V/W (elements), byte offsets of V, W1,
+// W3, W4, H1, H2, L, p}.
+void recycle_state_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, int64_t *out) {
+    char *const base = (char *)4096;
+    Carver c(base, (size_t)1 << 62);
+    RecyLayout R;
+    recy_layout(h, o, npts, c, R, o->io_host != 0);
+    auto off = [&](const void *p) { return (int64_t)((const char *)p - base); };
+    const int64_t v[11] = {R.L, R.KM, R.Ld, off(R.V), off(R.W1), off(R.W3), off(R.W4), off(R.H1), off(R.H2),
+                           off(R.Lf), off(R.p)};
+    for (int i = 0; i < 11; ++i) out[i] = v[i];
+}
+
 // Batch-zigzag visiting order (Sec. 2.3, eq. (batch)): column batches of b
 // points, batch-rows in a row-wise zigzag, each batch visited vertically.
 static std::vector<int> batch_zigzag(int64_t npts, int nx, int ny, int b) {
@@ -336,7 +350,7 @@ static cudaError_t solve_listed(pseudo_ctx *h, RecyLayout &R, double2 *buf, int 
     }
     launch_copy_listed<double2, float2>(buf, R.SB32, n, R.Wd, R.cols, ncols, 0, 0, r3, scale, LB_MAXM, 1, s);
     const int k0 = kp_begin(h, s);
-    cudaError_t e = launch_trsv32(adjoint ? h->L32 : h->U32, n, h->n_pad, adjoint, R.cols, R.zcol, ncols, nullptr,
+    cudaError_t e = solve32(h, adjoint, R.cols, R.zcol, ncols, nullptr,
                                   R.SB32, R.Wd, (float2 *)R.xs, s);
     kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncols), tri_bytes(n, ncols, 8, 8, 2), s);
     if (e != cudaSuccess) return e;

@@ -3,8 +3,8 @@
 // units in double-single arithmetic, and the correction is accumulated in
 // FP64.  The number of solves a column gets follows from its estimated
 // condition: the error contracts by about rho = c * kappa * u_32 per step with
-// kappa = (||T||_2 + |z|) / sigma, so a column gets the fewest k with
-// rho^k <= 1e-13 (at least 2, at most max_ir).  Columns are kept sorted by k,
+// kappa = (||T||_2 + |z|) / sigma, so a column gets the fewest k with rho^k
+// below its accuracy target (at least 2, at most max_ir).  Columns are kept sorted by k,
 // so the columns still refining at step `it` are a prefix of one list and
 // every launch covers exactly them.
 #include <algorithm>
@@ -27,11 +27,18 @@ void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<do
     const int S = (int)sig.size();
     if (S_total < S) S_total = S;
     std::vector<int> need(S_total, 0), perm(S);
-    const double u32 = 5.96e-8;
+    const double u32 = solve32_unit_roundoff(h);
     for (int c = 0; c < S; ++c) {
-        const double kappa = (h->norm2 + std::hypot(z[c].x, z[c].y)) / std::max(sig[c], 1e-300);
+        // The refined vector feeds a Rayleigh quotient whose error is quadratic
+        // in the vector error: a relative solve error d costs about (d / sigma)^2
+        // relative in sigma, so d = 1e-5 sigma / ||M(z)|| keeps sigma well inside
+        // 1e-8.
+        const double mz = h->norm2 + std::hypot(z[c].x, z[c].y);
+        const double sg = std::max(sig[c], 1e-300);
+        const double kappa = mz / sg;
         const double rho = std::min(0.5, 8.0 * kappa * u32);
-        int k = (int)std::ceil(std::log(1e-13) / std::log(rho));
+        const double target = std::max(1e-15, std::min(1e-8, 1e-5 * sg / mz));
+        int k = (int)std::ceil(std::log(target) / std::log(rho));
         need[c] = std::max(2, std::min(max_ir, k));
     }
     std::iota(perm.begin(), perm.end(), 0);
@@ -58,7 +65,7 @@ cudaError_t ir_solve_cols(pseudo_ctx *h, const IRBufs &b, int lower, const doubl
         launch_colnorm2(b.R64, n, S, b.mask, b.rn2, s);
         launch_scale_to32(b.R64, n, S, b.mask, b.rn2, b.D32, s);
         int k0 = kp_begin(h, s);
-        e = launch_trsv32(lower ? h->L32 : h->U32, n, h->n_pad, lower, b.perm, zc, cnt, nullptr, b.D32, S, b.xs, s);
+        e = solve32(h, lower, b.perm, zc, cnt, nullptr, b.D32, S, b.xs, s);
         kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, cnt), tri_bytes(n, cnt, 8, 8, 2), s);
         if (e != cudaSuccess) return e;
         launch_acc_from32(X, n, S, b.mask, b.rn2, b.D32, s);

@@ -234,7 +234,7 @@ static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower
 }
 
 // Column-group width of the solves: FP64 8 columns, FP32 16 columns per CTA.
-constexpr int R64 = 8, R32 = 8, NW_SOLVE = 8;
+constexpr int R64 = 8, R32 = 16, NW_SOLVE = 8;
 int trsv_group_width(int fp32) { return fp32 ? R32 : R64; }
 
 size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols) {

@@ -1,0 +1,345 @@
+// Multi-shift triangular solve on the 5th-generation tensor cores (tcgen05):
+// (T - z_c I) x_c = b_c or (T - z_c I)^H x_c = b_c for many columns c at once,
+// the FP32 form of the R(z)^{-1} / R(z)^{-*} applications (Alg. 3, the
+// inverse-Lanczos comparator and the refinement solves).
+//
+// The shift only touches the diagonal, so every off-diagonal block product
+// T_IK x_K is shared by all shifts and is a plain complex GEMM.  A CTA owns
+// NC right-hand sides and walks row panels of 128 rows (bottom-up for T,
+// top-down for T^H).  For a panel, D = sum_K T_IK X_K over the solved rows is
+// accumulated in TMEM by tcgen05.mma (kind::tf32, M = 128, N = 2 NC), then
+// the 128 x 128 shifted diagonal block is solved on the CUDA cores in FP32
+// (one row per thread, one column of the block per step).
+//
+// Complex as real: with A'' = [Re T_IK  Im T_IK] (128 x 2KC) and
+// B'' = [[Re X, Im X], [-Im X, Re X]] (2KC x 2NC), A'' B'' = [Re, Im] of T_IK X_K.
+// FP32 accuracy from TF32 units ("3xTF32"): every operand is split into
+// hi = tf32(v) and lo = tf32(v - hi), and A''B'' ~ hi hi + hi lo + lo hi.
+// A'' is split and packed once (at handle creation) in exactly the byte image
+// the MMA reads from shared memory, so a chunk is one bulk copy; B'' is built
+// from the solved columns by the CTA's threads.
+#include <cmath>
+
+#include "common.cuh"
+#include "driver.h"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace pseudo {
+
+namespace {
+constexpr int MB = 128;               // panel rows (MMA M)
+constexpr int KC = 16;                // complex K per chunk
+constexpr int KR = 2 * KC;            // real K per chunk
+constexpr int A_SPLIT = MB * KR;      // floats of one split of an A chunk
+constexpr int A_CHUNK = 2 * A_SPLIT;  // hi + lo
+constexpr int NTH = 128;
+
+__host__ __device__ __forceinline__ int64_t chunk_base(int64_t p) { return 4 * p * (p - 1); }
+}  // namespace
+
+int64_t tc_pack_floats(int n_pad) {
+    const int64_t P = n_pad / MB;
+    return chunk_base(P) * A_CHUNK;
+}
+int64_t tc_diag_elems(int n_pad) { return (int64_t)(n_pad / MB) * MB * MB; }
+
+// A'' chunks of every panel in processing order; see the file comment.
+__global__ void pack_tc_a_kernel(const double2 *__restrict__ T, int64_t ldT, int n, int n_pad, int lower,
+                                 float *__restrict__ out, int64_t total) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int P = n_pad / MB;
+    const int64_t qq = e / A_CHUNK;
+    const int w = (int)(e % A_CHUNK);
+    const int split = w / A_SPLIT, ww = w % A_SPLIT;
+    const int cmi = ww >> 5, r7 = (ww >> 2) & 7, k3 = ww & 3;
+    const int kb = cmi / (MB / 8), rb = cmi % (MB / 8);
+    const int m = rb * 8 + r7, kk = kb * 4 + k3;
+    int64_t p = (int64_t)((1.0 + sqrt(1.0 + (double)qq)) * 0.5);
+    while (p > 1 && chunk_base(p) > qq) --p;
+    while (chunk_base(p + 1) <= qq) ++p;
+    const int t = (int)(qq - chunk_base(p));
+    const int J = lower ? (int)p : P - 1 - (int)p;
+    const int k0 = lower ? KC * t : n_pad - KC * (t + 1);
+    const int row = J * MB + m, kc = k0 + (kk % KC), part = kk / KC;
+    double comp = 0.0;
+    if (row < n && kc < n) {
+        if (!lower) {
+            if (row <= kc) { const double2 v = T[(int64_t)kc * ldT + row]; comp = part ? v.y : v.x; }
+        } else {
+            if (kc <= row) { const double2 v = T[(int64_t)row * ldT + kc]; comp = part ? -v.y : v.x; }
+        }
+    }
+    const float f = (float)comp;
+    const float hi = tc::to_tf32(f);
+    out[e] = split ? tc::to_tf32(f - hi) : hi;
+}
+
+// Diagonal blocks, step-major: D[J][j][i] is the coefficient of x_j in row i
+// of block J: T(i, j) for the upper solve, conj(T(j, i)) for the lower one.
+__global__ void pack_tc_d_kernel(const double2 *__restrict__ T, int64_t ldT, int n, int n_pad,
+                                 float2 *__restrict__ DU, float2 *__restrict__ DL) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)(n_pad / MB) * MB * MB) return;
+    const int J = (int)(e / (MB * MB)), w = (int)(e % (MB * MB));
+    const int j = w / MB, i = w % MB;
+    const int ri = J * MB + i, rj = J * MB + j;
+    float2 u = make_float2(0.f, 0.f), l = make_float2(0.f, 0.f);
+    if (ri < n && rj < n) {
+        if (i <= j) { const double2 v = T[(int64_t)rj * ldT + ri]; u = make_float2((float)v.x, (float)v.y); }
+        if (j <= i) { const double2 v = T[(int64_t)ri * ldT + rj]; l = make_float2((float)v.x, (float)-v.y); }
+    }
+    DU[e] = u;
+    DL[e] = l;
+}
+
+void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, float *AL, float2 *DU, float2 *DL,
+                    cudaStream_t s) {
+    const int64_t tot = tc_pack_floats(n_pad);
+    if (tot > 0) {
+        const unsigned bl = (unsigned)((tot + 255) / 256);
+        note_launch(); pack_tc_a_kernel<<<bl, 256, 0, s>>>(T, ldT, n, n_pad, 0, AU, tot);
+        note_launch(); pack_tc_a_kernel<<<bl, 256, 0, s>>>(T, ldT, n, n_pad, 1, AL, tot);
+    }
+    const int64_t nd = tc_diag_elems(n_pad);
+    note_launch(); pack_tc_d_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(T, ldT, n, n_pad, DU, DL);
+}
+
+template <int NC>
+struct TcSmem {
+    static constexpr int NR = 2 * NC;            // real N of the MMA
+    static constexpr int B_SPLIT = NR * KR;      // floats
+    static constexpr size_t a_bytes = 2 * A_CHUNK * sizeof(float);
+    static constexpr size_t b_bytes = 2 * 2 * B_SPLIT * sizeof(float);
+    static constexpr size_t bytes = a_bytes + b_bytes + 128;  // + alignment slack
+    static constexpr uint32_t tmem_cols = NR < 32 ? 32 : NR;
+};
+
+template <int NC>
+__global__ void __launch_bounds__(NTH)
+trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
+               const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
+               const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err) {
+    using L = TcSmem<NC>;
+    constexpr int NR = L::NR;
+    constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_col[NC];
+    __shared__ float2 s_z[NC];
+    __shared__ float2 s_x[2][NC];
+
+    const int ncols = ncols_dev ? *ncols_dev : ncols_host;
+    const int g = blockIdx.x;
+    if (g * NC >= ncols) return;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float *sA = reinterpret_cast<float *>(smem_raw + ((128 - (tc::smem_u32(smem_raw) & 127)) & 127));
+    float *sB = sA + 2 * A_CHUNK;
+
+    if (tid < NC) {
+        const int pos = g * NC + tid;
+        int c = -1;
+        double2 z = make_double2(0.0, 0.0);
+        if (pos < ncols) { c = cols ? cols[pos] : pos; z = zc[c]; }
+        if (lower) z.y = -z.y;  // (T - zI)^H = T^H - conj(z) I
+        s_col[tid] = c;
+        s_z[tid] = make_float2((float)z.x, (float)z.y);
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_ld[0], 1);
+        tc::mbar_init(&bar_ld[1], 1);
+        tc::mbar_init(&bar_mma[0], 1);
+        tc::mbar_init(&bar_mma[1], 1);
+        tc::mbar_fence_init();
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&s_tmem, L::tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t sA0 = tc::smem_u32(sA), sB0 = tc::smem_u32(sB);
+    constexpr uint32_t idesc = tc::idesc_tf32(MB, NR);
+    float2 *xs = xs_all + (int64_t)g * n_pad * NC;
+    const int P = n_pad / MB;
+    uint32_t q = 0;          // chunks issued so far
+    int ld_pending = -1;     // chunk whose A load thread 0 has not yet waited for
+
+    for (int p = 0; p < P; ++p) {
+        const int J = lower ? p : P - 1 - p;
+        const int nch = 8 * p;
+        const float *Ap = Apack + chunk_base(p) * A_CHUNK;
+        for (int t = 0; t < nch; ++t, ++q) {
+            const int st = q & 1;
+            if (tid == 0 && !s_abort) {
+                if (q >= 2 && !tc::mbar_wait(&bar_mma[st], ((q >> 1) - 1) & 1)) {
+                    s_abort = 1;
+                } else {
+                    tc::mbar_expect_tx(&bar_ld[st], A_CHUNK * sizeof(float));
+                    tc::bulk_g2s(sA + st * A_CHUNK, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &bar_ld[st]);
+                    ld_pending = (int)q;
+                }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            {   // B'' of this chunk from the solved rows k0 .. k0 + KC - 1
+                const int k0 = lower ? KC * t : n_pad - KC * (t + 1);
+                constexpr int CPT = NC / 8;  // columns per thread (16 rows x 8 threads)
+                const int kl = tid >> 3, cb = (tid & 7) * CPT;
+                float *bh = sB + st * 2 * L::B_SPLIT, *bl = bh + L::B_SPLIT;
+                const float2 *src = xs + (int64_t)(k0 + kl) * NC + cb;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) {
+                    const float2 x = src[u];
+                    const int c = cb + u;
+                    const float v[4] = {x.x, -x.y, x.y, x.x};
+                    const int jj[4] = {c, c, NC + c, NC + c};
+                    const int kk[4] = {kl, KC + kl, kl, KC + kl};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float h = tc::to_tf32(v[e]);
+                        const int o = tc::cm_index(jj[e], kk[e], NR);
+                        bh[o] = h;
+                        bl[o] = tc::to_tf32(v[e] - h);
+                    }
+                }
+                tc::fence_async_smem();
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (!tc::mbar_wait(&bar_ld[st], (q >> 1) & 1)) {
+                    s_abort = 1;
+                } else {
+                    ld_pending = -1;
+                    tc::tc_fence_after();
+                    const uint32_t ah = sA0 + st * (A_CHUNK * 4), al = ah + A_SPLIT * 4;
+                    const uint32_t bh = sB0 + st * (2 * L::B_SPLIT * 4), bl = bh + L::B_SPLIT * 4;
+#pragma unroll
+                    for (int ks = 0; ks < KR / 8; ++ks) {
+                        const uint64_t dah = tc::smem_desc(ah + ks * 2 * LBO_A, LBO_A, 128);
+                        const uint64_t dal = tc::smem_desc(al + ks * 2 * LBO_A, LBO_A, 128);
+                        const uint64_t dbh = tc::smem_desc(bh + ks * 2 * LBO_B, LBO_B, 128);
+                        const uint64_t dbl = tc::smem_desc(bl + ks * 2 * LBO_B, LBO_B, 128);
+                        tc::mma_tf32(tmem, dah, dbh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+                        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+                    }
+                    tc::mma_commit(&bar_mma[st]);
+                }
+            }
+        }
+        // ---- epilogue: r = b - D, then the shifted diagonal block
+        if (tid == 0 && nch > 0 && !s_abort) {
+            const uint32_t ql = q - 1;
+            if (!tc::mbar_wait(&bar_mma[ql & 1], (ql >> 1) & 1)) s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        tc::tc_fence_after();
+        float d[32];
+        if (nch > 0) {
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), d);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) d[u] = 0.f;
+        }
+        const int i = tid, row = J * MB + i;
+        const float2 *DJ = Dblk + (int64_t)J * MB * MB;
+        float2 r[NC], dinv[NC];
+        const float2 tii = DJ[i * MB + i];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            float2 b = make_float2(0.f, 0.f);
+            if (row < n && s_col[c] >= 0) b = X[(int64_t)row * ldx + s_col[c]];
+            r[c] = make_float2(b.x - d[c], b.y - d[NC + c]);
+            dinv[c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+        }
+        if (!lower) {
+            for (int j = MB - 1; j >= 0; --j) {
+                if (i == j) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
+                }
+                __syncthreads();
+                if (i < j) {
+                    const float2 tij = DJ[j * MB + i];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                }
+            }
+        } else {
+            for (int j = 0; j < MB; ++j) {
+                if (i == j) {
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
+                }
+                __syncthreads();
+                if (i > j) {
+                    const float2 tij = DJ[j * MB + i];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float2 v = row < n ? r[c] : make_float2(0.f, 0.f);
+            xs[(int64_t)row * NC + c] = v;
+            if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    }
+    // ---- teardown (also after an abort: let copies and MMAs in flight finish)
+    if (tid == 0 && s_abort) {
+        if (ld_pending >= 0) tc::mbar_wait(&bar_ld[ld_pending & 1], (ld_pending >> 1) & 1, 100000000ull);
+        if (q > 0) tc::mbar_wait(&bar_mma[(q - 1) & 1], ((q - 1) >> 1) & 1, 100000000ull);
+        atomicExch(err, 1);
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, L::tmem_cols);
+}
+
+constexpr int NC_TC = 16;
+int trsv_tc_group_width() { return NC_TC; }
+
+cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                           const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
+    using L = TcSmem<NC_TC>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(trsv_tc_kernel<NC_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        attr = true;
+    }
+    const int grid = (ncols + NC_TC - 1) / NC_TC;
+    if (grid == 0) return cudaSuccess;
+    note_launch();
+    trsv_tc_kernel<NC_TC><<<grid, NTH, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
+                                                      h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs,
+                                                      h->dev_err);
+    return cudaGetLastError();
+}
+
+cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                    const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
+    // both kernels take 16 columns per CTA, so they share one scratch size
+    static_assert(NC_TC == 16, "scratch of the tensor-core solve is sized like the CUDA-core one");
+    if (h->fp32_solver == 0 && h->tcA_U)
+        return launch_trsv_tc(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+    return launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+}
+
+// 3xTF32 products carry about 2^-22 relative error against FP32's 2^-24
+double solve32_unit_roundoff(const pseudo_ctx *h) {
+    return (h->fp32_solver == 0 && h->tcA_U) ? 2.4e-7 : 5.96e-8;
+}
+
+}  // namespace pseudo

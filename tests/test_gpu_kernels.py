@@ -34,12 +34,39 @@ def test_solve_fp64_and_mixed(n, ncols, adjoint):
     got = X.cpu().numpy()
     rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
     assert rel.max() < 1e-12, rel.max()
-    X = torch.from_numpy(B.copy()).cuda()
-    h.solve(X, z, adjoint=adjoint, precision=p.MIXED)
-    got = X.cpu().numpy()
-    rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
-    assert rel.max() < 2e-4, rel.max()
+    for prec in (p.MIXED, p.MIXED_CUDACORE):
+        X = torch.from_numpy(B.copy()).cuda()
+        h.solve(X, z, adjoint=adjoint, precision=prec)
+        got = X.cpu().numpy()
+        rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+        assert rel.max() < 2e-4, (prec, rel.max())
     h.close()
+
+
+@pytest.mark.parametrize("n", [127, 128, 129, 300, 520])
+@pytest.mark.parametrize("ncols", [1, 16, 45])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_solve_fp32_tensor_cores(n, ncols, adjoint):
+    """The tcgen05 solve (3xTF32 off-diagonal blocks, 128-row panels) across
+    several panels with a ragged last panel and partial 16-column groups: its
+    error against the oracle stays within a few FP32 units of the condition
+    number, like the CUDA-core FP32 solve."""
+    import torch
+
+    import paper_2606_26785_b300 as p
+
+    T, z, B = _case(n, ncols, 7000 + 1000 * n + ncols)
+    h = p.Pseudo(T)
+    ref = steps.shifted_solve(T, z, B, adjoint)
+    errs = {}
+    for prec in (p.MIXED, p.MIXED_CUDACORE):
+        X = torch.from_numpy(B.copy()).cuda()
+        h.solve(X, z, adjoint=adjoint, precision=prec)
+        got = X.cpu().numpy()
+        errs[prec] = (np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)).max()
+    h.close()
+    assert errs[p.MIXED] < 2e-5, errs
+    assert errs[p.MIXED] < 30 * errs[p.MIXED_CUDACORE] + 1e-6, errs
 
 
 @pytest.mark.parametrize("n", [1, 3, 65, 130])
