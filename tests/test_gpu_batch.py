@@ -68,11 +68,9 @@ def test_multi_matrix_workload_sampled():
     on the first 16 matrices of its sequence, in one batched call in mixed
     precision; stored oracle values (tests/golden/batch16_samples.json,
     written by tests/golden/make_batch_samples.py) at 24 points of the 8
-    smallest matrices, and an upper-bound check at every point: sigma_min is
-    at most the distance from z to the nearest eigenvalue times the norm of
-    the eigenvalue's Schur-basis column bound, so here only sigma <= |z - t_ii|
-    over all i is asserted (T - zI has a zero singular direction when z = t_ii
-    and sigma_min(T - zI) <= min_i |t_ii - z| holds for triangular T)."""
+    smallest matrices, and at every point the bound sigma_min(T - zI) <=
+    min_i |t_ii - z| (the smallest singular value never exceeds the modulus
+    of an eigenvalue)."""
     import json
     from pathlib import Path
 
