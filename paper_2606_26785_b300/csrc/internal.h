@@ -138,7 +138,7 @@ template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
                          const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
                          int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
-                         int *fin_conv, const double2 *v0, cudaStream_t s);
+                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s);
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,

@@ -32,6 +32,7 @@ struct LancLayout {
     double *nrm2 = nullptr, *alpha_acc = nullptr;   // per-slot partial sums
     int *jv = nullptr, *active = nullptr, *cols = nullptr, *cnt = nullptr, *convd = nullptr, *pt = nullptr;
     int *counters = nullptr, *nbad = nullptr;
+    int4 *hwork = nullptr;  // harvest lists (converged, refilled), 2 S entries
     double2 *zslot = nullptr, *startv = nullptr;
     // finished points (capacity F = 2S, leading dimension F)
     double2 *Ufin = nullptr, *fin_z = nullptr, *Y = nullptr, *NX = nullptr, *X64 = nullptr, *R64 = nullptr,
@@ -92,6 +93,7 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     L.convd = c.get<int>(S);
     L.pt = c.get<int>(S);
     L.counters = c.get<int>(4);
+    L.hwork = c.get<int4>(2 * S);
     L.nbad = c.get<int>(4);
     L.zslot = c.get<double2>(S);
     L.startv = c.get<double2>(n);
@@ -209,11 +211,11 @@ static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const 
         if (L.fp32)
             launch_slot_harvest<float>((float2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd, L.pt,
                                        L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
-                                       L.fin_theta, L.fin_conv, L.startv, s);
+                                       L.fin_theta, L.fin_conv, L.startv, L.hwork, s);
         else
             launch_slot_harvest<double>((double2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd,
                                         L.pt, L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
-                                        L.fin_theta, L.fin_conv, L.startv, s);
+                                        L.fin_theta, L.fin_conv, L.startv, L.hwork, s);
     };
     harvest();
     int host[4];

@@ -522,68 +522,79 @@ __global__ void slot_tridiag_kernel(int S, int mmax, const double *__restrict__ 
     }
 }
 
-// Harvest finished slots (Ritz vector into the finished buffer, ld F) and
-// refill finished or empty slots with the next points.
-template <typename real>
-__global__ void __launch_bounds__(ORTH_WARPS * 32)
-slot_harvest_kernel(cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, int mmax, const double *__restrict__ svec,
-                    int *__restrict__ jv, int *__restrict__ active, const double *__restrict__ theta,
-                    const int *__restrict__ convd, int *__restrict__ pt, double2 *__restrict__ zslot,
-                    const double2 *__restrict__ zall, int npts, int *__restrict__ counters, double2 *__restrict__ Ufin,
-                    int F, int *__restrict__ fin_pt, double2 *__restrict__ fin_z, double *__restrict__ fin_theta,
-                    int *__restrict__ fin_conv, const double2 *__restrict__ v0) {
-    __shared__ int s_dest[32], s_next[32], s_state[32];
-    __shared__ int any;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * 32 + lane;
-    if (threadIdx.x == 0) any = 0;
-    __syncthreads();
-    if (warp == 0) {
-        const int st = c < S ? active[c] : 0;
-        int dest = -1, nxt = -1;
-        if (st == 2) dest = atomicAdd(&counters[1], 1);
-        if (st == 2 || st == 3) nxt = atomicAdd(&counters[0], 1);
-        s_state[lane] = st;
-        s_dest[lane] = dest;
-        s_next[lane] = nxt;
-        if (st >= 2) atomicOr(&any, 1);
-    }
-    __syncthreads();
-    if (!any) return;
-    const int st = s_state[lane], dest = s_dest[lane], nxt = s_next[lane];
+// Bookkeeping of the harvest, one thread per slot: a converged slot (state 2)
+// gets its place in the finished buffer and is listed for its Ritz vector; a
+// converged or empty slot (state 3) takes the next point and is listed for the
+// refill of its start vector.
+__global__ void slot_book_kernel(int S, int *__restrict__ jv, int *__restrict__ active,
+                                 const double *__restrict__ theta, const int *__restrict__ convd, int *__restrict__ pt,
+                                 double2 *__restrict__ zslot, const double2 *__restrict__ zall, int npts,
+                                 int *__restrict__ counters, int *__restrict__ fin_pt, double2 *__restrict__ fin_z,
+                                 double *__restrict__ fin_theta, int *__restrict__ fin_conv, int4 *__restrict__ work) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= S) return;
+    const int st = active[c];
     if (st == 2) {
-        const int k = jv[c] + 1;
-        for (int i = warp; i < n; i += ORTH_WARPS) {
-            double ur = 0.0, ui = 0.0;
-            for (int t = 0; t < k; ++t) {
-                const double sv = svec[(int64_t)c * mmax + t];
-                const cx_t<real> q = Q[(int64_t)t * qs + (int64_t)i * S + c];
-                ur += sv * (double)q.x;
-                ui += sv * (double)q.y;
-            }
-            Ufin[(int64_t)i * F + dest] = make_double2(ur, ui);
-        }
-        if (warp == 0) {
-            fin_pt[dest] = pt[c];
-            fin_z[dest] = zslot[c];
-            fin_theta[dest] = theta[c];
-            fin_conv[dest] = convd[c];
-        }
+        const int dest = atomicAdd(&counters[1], 1);
+        fin_pt[dest] = pt[c];
+        fin_z[dest] = zslot[c];
+        fin_theta[dest] = theta[c];
+        fin_conv[dest] = convd[c];
+        work[atomicAdd(&counters[2], 1)] = make_int4(c, dest, jv[c] + 1, 0);
     }
-    __syncthreads();  // every read of slot c's basis is done before the refill overwrites q_0
     if (st == 2 || st == 3) {
+        const int nxt = atomicAdd(&counters[0], 1);
         if (nxt < npts) {
-            for (int i = warp; i < n; i += ORTH_WARPS)
-                Q[(int64_t)i * S + c] = mk<real>((real)v0[i].x, (real)v0[i].y);
-            if (warp == 0) {
-                pt[c] = nxt;
-                zslot[c] = zall[nxt];
-                jv[c] = 0;
-                active[c] = 1;
-            }
-        } else if (warp == 0) {
+            pt[c] = nxt;
+            zslot[c] = zall[nxt];
+            jv[c] = 0;
+            active[c] = 1;
+            work[S + atomicAdd(&counters[3], 1)] = make_int4(c, 0, 0, 0);
+        } else {
             active[c] = 0;
         }
+    }
+}
+
+// Ritz vectors of the listed slots: U[:, dest] = Q_{0:k} svec, one thread per
+// (slot, row); the basis of a slot is strided by S, so this is a gather with
+// many independent loads in flight.
+template <typename real>
+__global__ void __launch_bounds__(256)
+slot_ritz_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, int mmax, const double *__restrict__ svec,
+                 const int4 *__restrict__ work, const int *__restrict__ cnt, double2 *__restrict__ Ufin, int F) {
+    const int64_t total = (int64_t)(*cnt) * n;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int4 e = work[w / n];
+        const int i = (int)(w % n), c = e.x, k = e.z;
+        const cx_t<real> *q = Q + (int64_t)i * S + c;
+        const double *sv = svec + (int64_t)c * mmax;
+        real ur = 0, ui = 0, vr = 0, vi = 0;
+        int t = 0;
+        for (; t + 1 < k; t += 2) {
+            const cx_t<real> a = q[(int64_t)t * qs], b = q[(int64_t)(t + 1) * qs];
+            const real sa = (real)sv[t], sb = (real)sv[t + 1];
+            ur += sa * a.x; ui += sa * a.y;
+            vr += sb * b.x; vi += sb * b.y;
+        }
+        if (t < k) {
+            const cx_t<real> a = q[(int64_t)t * qs];
+            const real sa = (real)sv[t];
+            ur += sa * a.x; ui += sa * a.y;
+        }
+        Ufin[(int64_t)i * F + e.y] = make_double2((double)(ur + vr), (double)(ui + vi));
+    }
+}
+
+// Start vectors of the refilled slots.
+template <typename real>
+__global__ void __launch_bounds__(256)
+slot_refill_kernel(cx_t<real> *__restrict__ Q, int n, int S, const int4 *__restrict__ work, const int *__restrict__ cnt,
+                   const double2 *__restrict__ v0) {
+    const int64_t total = (int64_t)(*cnt) * n;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int c = work[w / n].x, i = (int)(w % n);
+        Q[(int64_t)i * S + c] = mk<real>((real)v0[i].x, (real)v0[i].y);
     }
 }
 
@@ -647,11 +658,18 @@ template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
                          const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
                          int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
-                         int *fin_conv, const double2 *v0, cudaStream_t s) {
-    note_launch(); slot_harvest_kernel<real><<<(S + 31) / 32, ORTH_WARPS * 32, 0, s>>>(Q, qs, n, S, mmax, svec, jv, active, theta,
-                                                                                    convd, pt, zslot, zall, npts,
-                                                                                    counters, Ufin, F, fin_pt, fin_z,
-                                                                                    fin_theta, fin_conv, v0);
+                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s) {
+    cudaMemsetAsync(counters + 2, 0, 2 * sizeof(int), s);
+    note_launch();
+    slot_book_kernel<<<(S + 255) / 256, 256, 0, s>>>(S, jv, active, theta, convd, pt, zslot, zall, npts, counters,
+                                                     fin_pt, fin_z, fin_theta, fin_conv, work);
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    note_launch();
+    slot_ritz_kernel<real><<<nsm * 8, 256, 0, s>>>(Q, qs, n, S, mmax, svec, work, counters + 2, Ufin, F);
+    note_launch();
+    slot_refill_kernel<real><<<nsm * 8, 256, 0, s>>>(Q, n, S, work + S, counters + 3, v0);
 }
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
@@ -701,10 +719,10 @@ template void launch_slot_orth<double>(double2 *, int64_t, double2 *, int, int, 
                                        double *, int, cudaStream_t);
 template void launch_slot_harvest<float>(float2 *, int64_t, int, int, int, const double *, int *, int *, const double *,
                                          const int *, int *, double2 *, const double2 *, int, int *, double2 *, int,
-                                         int *, double2 *, double *, int *, const double2 *, cudaStream_t);
+                                         int *, double2 *, double *, int *, const double2 *, int4 *, cudaStream_t);
 template void launch_slot_harvest<double>(double2 *, int64_t, int, int, int, const double *, int *, int *,
                                           const double *, const int *, int *, double2 *, const double2 *, int, int *,
-                                          double2 *, int, int *, double2 *, double *, int *, const double2 *,
+                                          double2 *, int, int *, double2 *, double *, int *, const double2 *, int4 *,
                                           cudaStream_t);
 
 }  // namespace pseudo
