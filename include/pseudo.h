@@ -58,7 +58,7 @@ enum {
 
 enum { PSEUDO_INVLANC = 0, PSEUDO_RECYCLE = 1 };
 enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
-/* pseudo_solve only: the FP32 solve on the CUDA cores instead of the tensor cores */
+/* pseudo_solve / pseudo_matvec only: the CUDA-core kernels instead of the tensor-core ones */
 enum { PSEUDO_MIXED_CUDACORE = 2 };
 
 /* per-point flags (flags_out) */
@@ -232,15 +232,21 @@ int64_t pseudo_launch_count(void);
  * pseudo_matvec: Y[:, c] <- B[:, c] - (T - z_c I)^{op} X[:, c] (subtract = 1) or
  *   Y[:, c] <- (T - z_c I)^{op} X[:, c] (subtract = 0, B ignored and may be NULL); the
  *   refinement residual of a shifted solve and the products T V, T^H V of Alg. 2.
- *   precision PSEUDO_FP64: IEEE double arithmetic; PSEUDO_MIXED: double-single
- *   arithmetic on the FP32 units (T split into two FP32 planes, exact products and
- *   two-sums; relative error about 2^-46).
- *   X, Y, B device row-major n x ncols complex; Y must not alias X. z may be NULL (z = 0). */
+ *   precision PSEUDO_FP64: IEEE double arithmetic; PSEUDO_MIXED: on the tensor cores,
+ *   T and X split into 7 exact bf16 slices each (per-row / per-column power-of-two
+ *   scaling), slice products accumulated exactly per level in FP32 and summed in
+ *   double-single (about 2^-50 relative to the row and column maxima);
+ *   PSEUDO_MIXED_CUDACORE: double-single arithmetic on the FP32 units (T split into
+ *   two FP32 planes, exact products and two-sums; relative error about 2^-46).
+ *   X, Y, B device row-major n x ncols complex; Y must not alias X. z may be NULL (z = 0).
+ *   workspace : device, >= pseudo_matvec_workspace_bytes bytes (used by PSEUDO_MIXED). */
+int pseudo_matvec_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
 int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
 int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
                  int precision, void *workspace, size_t workspace_bytes, void *stream);
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
-                  const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision, void *stream);
+                  const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision,
+                  void *workspace, size_t workspace_bytes, void *stream);
 
 /* pseudo_solve_noalloc: the FP64 form of pseudo_solve without a workspace, for
  * callers that cannot allocate device memory (a process that reserved its whole

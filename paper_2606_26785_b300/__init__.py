@@ -191,14 +191,18 @@ class Pseudo:
         return X
 
     def matvec(self, X, z=None, B=None, adjoint: bool = False, precision: int = FP64, stream=None):
-        """Y = (T - zI)^{op} X, or B - (T - zI)^{op} X when B is given; FP64 or
-        double-single (precision=MIXED) arithmetic."""
+        """Y = (T - zI)^{op} X, or B - (T - zI)^{op} X when B is given; FP64,
+        double-single accurate on the tensor cores (precision=MIXED) or on the
+        CUDA cores (precision=MIXED_CUDACORE)."""
         torch = _torch()
         ncols = X.shape[1]
         Y = torch.empty_like(X)
         zt = None if z is None else torch.as_tensor(z).to(device="cuda", dtype=torch.complex128).contiguous()
+        b = ctypes.c_size_t()
+        check(self._lib.pseudo_matvec_workspace_bytes(self._h, ncols, ctypes.byref(b)))
+        ws = torch.empty(b.value, dtype=torch.uint8, device="cuda")
         check(self._lib.pseudo_matvec(self._h, _ptr(X), _ptr(B), _ptr(Y), _ptr(zt), ncols, int(adjoint),
-                                      int(B is not None), int(precision), _stream_ptr(stream)))
+                                      int(B is not None), int(precision), _ptr(ws), b.value, _stream_ptr(stream)))
         return Y
 
 

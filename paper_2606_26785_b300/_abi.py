@@ -17,7 +17,7 @@ EXPORTED = (
     "pseudo_opts_default", "pseudo_create", "pseudo_workspace_bytes", "pseudo_grid", "pseudo_stats",
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
     "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count", "pseudo_recycle_state_layout",
-    "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch",
+    "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch", "pseudo_matvec_workspace_bytes",
 )
 
 
@@ -87,7 +87,8 @@ def load(build_if_missing: bool = True):
     lib.pseudo_launch_count.argtypes = []
     lib.pseudo_launch_count.restype = ctypes.c_int64
     lib.pseudo_kernel_stats.argtypes = [vp, ci, ctypes.POINTER(KStat)]
-    lib.pseudo_matvec.argtypes = [vp, vp, vp, vp, vp, i64, ci, ci, ci, vp]
+    lib.pseudo_matvec.argtypes = [vp, vp, vp, vp, vp, i64, ci, ci, ci, vp, ctypes.c_size_t, vp]
+    lib.pseudo_matvec_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_grid_batch_workspace_bytes.argtypes = [vp, ci, vp, po, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_grid_batch.argtypes = [vp, ci, vp, vp, vp, ci, po, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     for name in EXPORTED:

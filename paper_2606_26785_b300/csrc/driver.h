@@ -60,6 +60,10 @@ struct pseudo_ctx {
     float *tcA_U = nullptr, *tcA_L = nullptr;
     float2 *tcD_U = nullptr, *tcD_L = nullptr;
     int *dev_err = nullptr;
+    // tensor-core double-single products: 7 bf16 slices of T and T^H per
+    // (64-row tile, 16-column chunk) image, and the per-row scale exponents
+    void *ozA_U = nullptr, *ozA_L = nullptr;
+    int *ozE_U = nullptr, *ozE_L = nullptr;
     int fp32_solver = 0;                     // 0 tensor cores, 1 CUDA cores
     double norm_fro = 0.0, norm2 = 0.0;      // ||T||_F and a 2-norm estimate
     pseudo_stats_t stats;
@@ -117,7 +121,10 @@ namespace pseudo {
 // of X used by the double-single kernel.
 inline cudaError_t trmv_hp(pseudo_ctx *h, bool ds, int lower, const int *cols, const double2 *zc, int ncols,
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
-                           int subtract, cudaStream_t s, float2 *xh = nullptr, float2 *xl = nullptr) {
+                           int subtract, cudaStream_t s, float2 *xh = nullptr, float2 *xl = nullptr,
+                           void *oz = nullptr) {
+    if (ds && oz && h->ozA_U)
+        return launch_trmv_oz(h, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy, subtract, oz, s);
     if (ds)
         return launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, cols, zc,
                               ncols, X, ldx, B, ldb, Y, ldy, subtract, s, xh, xl);
@@ -135,6 +142,7 @@ struct IRBufs {
     int *mask, *need, *perm;
     float2 *xs;       // FP32 solve scratch for S columns
     float2 *xh, *xl;  // double-single split of X, n x S
+    void *oz;         // tensor-core product scratch (oz_scratch_bytes for S columns) or NULL
 };
 struct IRPlan {
     std::vector<int> cnt;  // cnt[it]: columns still refining at step it

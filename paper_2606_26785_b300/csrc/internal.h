@@ -45,6 +45,14 @@ cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const doubl
                     const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
 // unit roundoff of the FP32 solve in use (for the refinement plan)
 double solve32_unit_roundoff(const pseudo_ctx *h);
+// trmv_oz.cu: double-single-accurate shifted products on the tensor cores
+int64_t oz_a_elems(int n_pad);
+size_t oz_scratch_bytes(int n_pad, int64_t ncols);
+void launch_pack_oz(const double2 *T, int64_t ldT, int n, int n_pad, void *AU, void *AL, int *exU, int *exL,
+                    cudaStream_t s);
+cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                           const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
+                           int subtract, void *scratch, cudaStream_t s);
 }  // namespace pseudo
 
 namespace pseudo {

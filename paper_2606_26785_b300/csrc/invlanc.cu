@@ -40,6 +40,7 @@ struct LancLayout {
     double *fin_theta = nullptr, *s2 = nullptr, *rr = nullptr, *rn2 = nullptr, *eps = nullptr;
     int *fin_pt = nullptr, *fin_conv = nullptr, *mask = nullptr, *need = nullptr, *perm = nullptr;
     float2 *D32 = nullptr, *xs32 = nullptr, *xh = nullptr, *xl = nullptr;
+    void *oz = nullptr;  // tensor-core product scratch for F columns
     double2 *z_dev = nullptr;
     double *sig_dev = nullptr, *res_dev = nullptr;
     int32_t *flags_dev = nullptr;
@@ -117,6 +118,7 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
         L.xs32 = (float2 *)c.take(trsv_scratch_bytes(1, h->n_pad, F));
         L.xh = c.get<float2>(n * F);
         L.xl = c.get<float2>(n * F);
+        L.oz = c.take(oz_scratch_bytes(h->n_pad, F));
         L.need = c.get<int>(F);
         L.perm = c.get<int>(F);
         L.fb_list = c.get<int>(npts);
@@ -154,7 +156,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     launch_fill_int(L.mask, P, 1, s);
     launch_normalize(L.Ufin, n, F, L.mask, s);
     if (L.fp32) {
-        IRBufs ib{L.R64, L.D32, L.rn2, L.mask, L.need, L.perm, L.xs32, L.xh, L.xl};
+        IRBufs ib{L.R64, L.D32, L.rn2, L.mask, L.need, L.perm, L.xs32, L.xh, L.xl, L.oz};
         IRPlan plan;
         {
             std::vector<double> th(P), sg(P);
@@ -176,8 +178,8 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     // Rayleigh quotient and residual of the returned vectors
     const int kc = L.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
     int k0 = kp_begin(h, s);
-    trmv_hp(h, L.fp32, 0, nullptr, L.fin_z, P, L.Ufin, F, nullptr, F, L.Y, F, 0, s, L.xh, L.xl);
-    trmv_hp(h, L.fp32, 1, nullptr, L.fin_z, P, L.Y, F, nullptr, F, L.NX, F, 0, s, L.xh, L.xl);
+    trmv_hp(h, L.fp32, 0, nullptr, L.fin_z, P, L.Ufin, F, nullptr, F, L.Y, F, 0, s, L.xh, L.xl, L.oz);
+    trmv_hp(h, L.fp32, 1, nullptr, L.fin_z, P, L.Y, F, nullptr, F, L.NX, F, 0, s, L.xh, L.xl, L.oz);
     kp_end(h, k0, kc, 2 * tri_flops(n, P), 2 * tri_bytes(n, P, 16, 16, 2), s);
     h->stats.mv_M_fp64_refine += 2 * (int64_t)P;
     launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);

@@ -113,6 +113,10 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaMalloc(&h->tcD_U, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_U"));
     if ((e = cudaMalloc(&h->tcD_L, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_L"));
     if ((e = cudaMalloc(&h->dev_err, sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc dev_err"));
+    if ((e = cudaMalloc(&h->ozA_U, oz_a_elems(h->n_pad) * 2 + 256)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozA_U"));
+    if ((e = cudaMalloc(&h->ozA_L, oz_a_elems(h->n_pad) * 2 + 256)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozA_L"));
+    if ((e = cudaMalloc(&h->ozE_U, h->n_pad * sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozE_U"));
+    if ((e = cudaMalloc(&h->ozE_L, h->n_pad * sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozE_L"));
     if ((e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), s)) != cudaSuccess) return fail(cuda_err(e, "memset"));
     if ((e = cudaMalloc(&bad, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if ((e = cudaMalloc(&dsum, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
@@ -125,6 +129,7 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     }
     launch_pack_panels(Td, ldT, (int)n, h->n_pad, h->U64, h->L64, h->U32, h->L32, s);
     launch_pack_tc(Td, ldT, (int)n, h->n_pad, h->tcA_U, h->tcA_L, h->tcD_U, h->tcD_L, s);
+    launch_pack_oz(Td, ldT, (int)n, h->n_pad, h->ozA_U, h->ozA_L, h->ozE_U, h->ozE_L, s);
     launch_pack_lo(h->U64, h->U32, h->U32lo, psz, s);
     launch_pack_lo(h->L64, h->L32, h->L32lo, psz, s);
     cudaMemsetAsync(bad, 0, sizeof(int), s);
@@ -185,6 +190,10 @@ void pseudo_destroy(pseudo_handle h) {
     cudaFree(h->tcD_U);
     cudaFree(h->tcD_L);
     cudaFree(h->dev_err);
+    cudaFree(h->ozA_U);
+    cudaFree(h->ozA_L);
+    cudaFree(h->ozE_U);
+    cudaFree(h->ozE_L);
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     delete h;
 }
@@ -277,26 +286,38 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
     return PSEUDO_OK;
 }
 
+int pseudo_matvec_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) {
+    if (!h || !bytes || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    *bytes = oz_scratch_bytes(h->n_pad, ncols) + 256;
+    return PSEUDO_OK;
+}
+
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y, const pseudo_c64 *z,
-                  int64_t ncols, int adjoint, int subtract, int precision, void *stream) {
+                  int64_t ncols, int adjoint, int subtract, int precision, void *workspace, size_t workspace_bytes,
+                  void *stream) {
     clear_err();
     if (!h || !X || !Y || ncols < 0 || (subtract && !B)) return set_err(PSEUDO_ERR_ARG, "bad argument");
-    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED) return set_err(PSEUDO_ERR_ARG, "bad precision");
+    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE)
+        return set_err(PSEUDO_ERR_ARG, "bad precision");
     if (ncols > (1 << 18)) return set_err(PSEUDO_ERR_ARG, "ncols too large");
     if ((const void *)X == (const void *)Y) return set_err(PSEUDO_ERR_ARG, "Y must not alias X");
     if (ncols == 0) return PSEUDO_OK;
+    if (precision == PSEUDO_MIXED) {
+        size_t need = 0;
+        pseudo_matvec_workspace_bytes(h, ncols, &need);
+        if (!workspace || workspace_bytes < need) return set_err(PSEUDO_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+    }
     const int lower = adjoint ? 1 : 0;
-    cudaError_t e;
-    if (precision == PSEUDO_FP64)
-        e = launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
-                          nullptr, (const double2 *)X, ncols, (const double2 *)B, ncols, (double2 *)Y, ncols, subtract,
-                          (cudaStream_t)stream);
-    else
-        e = launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, nullptr,
-                           (const double2 *)z, (int)ncols, (const double2 *)X, ncols, (const double2 *)B, ncols,
-                           (double2 *)Y, ncols, subtract, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = trmv_hp(h, precision != PSEUDO_FP64, lower, nullptr, (const double2 *)z, (int)ncols,
+                                  (const double2 *)X, ncols, (const double2 *)B, ncols, (double2 *)Y, ncols, subtract,
+                                  s, nullptr, nullptr, precision == PSEUDO_MIXED ? workspace : nullptr);
     if (e != cudaSuccess) return cuda_err(e, "pseudo_matvec");
     h->stats.mv_M += ncols;
+    if (precision == PSEUDO_MIXED) {
+        const int rc = check_dev_err(h, s);
+        if (rc) return rc;
+    }
     return PSEUDO_OK;
 }
 

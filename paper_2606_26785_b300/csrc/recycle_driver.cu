@@ -304,7 +304,7 @@ static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int poli
     const int n = h->n;
     cudaError_t e = cudaSuccess;
     if (polish) {
-        IRBufs ib{R.R64, R.D32, R.rn2, R.mask, R.need, R.perm, (float2 *)R.xs, R.xh, R.xl};
+        IRBufs ib{R.R64, R.D32, R.rn2, R.mask, R.need, R.perm, (float2 *)R.xs, R.xh, R.xl, nullptr};
         IRPlan plan;
         {
             std::vector<double> xi((size_t)R.B * LB_MAXM), sg(cnt);

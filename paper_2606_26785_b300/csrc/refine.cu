@@ -72,7 +72,7 @@ cudaError_t ir_solve_cols(pseudo_ctx *h, const IRBufs &b, int lower, const doubl
         h->stats.sv_R += cnt;
         if (next > 0) {
             k0 = kp_begin(h, s);
-            e = trmv_hp(h, true, lower, b.perm, zc, next, X, S, B, S, b.R64, S, 1, s, b.xh, b.xl);
+            e = trmv_hp(h, true, lower, b.perm, zc, next, X, S, B, S, b.R64, S, 1, s, b.xh, b.xl, b.oz);
             kp_end(h, k0, PSEUDO_K_TRMV_DS, tri_flops(n, next), tri_bytes(n, next, 16, 16, 3), s);
             if (e != cudaSuccess) return e;
             h->stats.mv_M_fp64_refine += next;

@@ -245,6 +245,13 @@ size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols) {
 
 cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
                           int ncols, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs, cudaStream_t s) {
+    // FP64 runs at 1/62 of FP32 here, so a few columns must still spread over
+    // many SMs: narrower column groups when the launch is small (the scratch
+    // of 8-column groups covers them)
+    if (ncols <= 296)
+        return trsv_launch<double, 1, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+    if (ncols <= 1184)
+        return trsv_launch<double, 2, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return trsv_launch<double, R64, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
 }
 cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,

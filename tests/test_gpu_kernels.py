@@ -89,25 +89,36 @@ def test_matvec_fp64(n, adjoint):
     h.close()
 
 
-@pytest.mark.parametrize("n", [3, 65, 257])
+@pytest.mark.parametrize("n", [3, 65, 257, 300])
+@pytest.mark.parametrize("ncols", [6, 64, 131])
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_matvec_double_single(n, adjoint):
-    """double-single product: relative error near 2^-46, far below FP32's."""
+def test_matvec_double_single(n, ncols, adjoint):
+    """double-single accurate products: the tensor-core slicing (PSEUDO_MIXED)
+    and the CUDA-core double-single kernel, relative error near 2^-46, far
+    below FP32's, across several 64-row tiles, ragged tails, partial
+    64-column tiles and a column scaled by 1e-9 (per-column exponents)."""
     import torch
 
     import paper_2606_26785_b300 as p
 
-    T, z, B = _case(n, 6, 11 + n)
+    T, z, B = _case(n, ncols, 11 + n + ncols)
     rng = np.random.default_rng(n + 1)
-    X = rng.standard_normal((n, 6)) + 1j * rng.standard_normal((n, 6))
+    X = rng.standard_normal((n, ncols)) + 1j * rng.standard_normal((n, ncols))
+    X[:, 0] *= 1e-9
     h = p.Pseudo(T)
     Xt, Bt = torch.from_numpy(X).cuda(), torch.from_numpy(B).cuda()
     ref = steps.shifted_matvec(T, z, X, adjoint)
-    Y = h.matvec(Xt, z=z, adjoint=adjoint, precision=p.MIXED).cpu().numpy()
-    scale = np.abs(np.triu(T)).sum(axis=1 if not adjoint else 0).max() * np.abs(X).max() + 1
-    assert np.max(np.abs(Y - ref)) <= 64 * n * 2.0 ** -46 * scale
-    R = h.matvec(Xt, z=z, B=Bt, adjoint=adjoint, precision=p.MIXED).cpu().numpy()
-    assert np.max(np.abs(R - (B - ref))) <= 64 * n * 2.0 ** -46 * scale
+    # per column: sum_k |T_ik| |x_k| bounds the rounding of any summation order
+    Ta = np.abs(np.triu(T))
+    bound = ((Ta.T if adjoint else Ta) @ np.abs(X)).max(axis=0) + np.abs(z) * np.abs(X).max(axis=0)
+    for prec in (p.MIXED, p.MIXED_CUDACORE):
+        Y = h.matvec(Xt, z=z, adjoint=adjoint, precision=prec).cpu().numpy()
+        err = np.abs(Y - ref).max(axis=0) / bound
+        assert err.max() <= 64 * 2.0 ** -46, (prec, err.max())
+        R = h.matvec(Xt, z=z, B=Bt, adjoint=adjoint, precision=prec).cpu().numpy()
+        err = np.abs(R - (B - ref)).max(axis=0) / bound
+        assert err.max() <= 64 * 2.0 ** -46, (prec, err.max())
+    h.close()
     h.close()
 
 
