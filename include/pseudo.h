@@ -90,7 +90,7 @@ typedef struct {
     double rtol;        /* accuracy target on sigma: points are accepted/converged only when
                            the a-posteriori relative error estimate is <= rtol/4; 0 = paper
                            tests only */
-    int maxiter_lanczos; /* Lanczos steps cap (<= 120) */
+    int maxiter_lanczos; /* Lanczos steps cap (1 .. 64) */
     int maxiter_lobpcg;  /* LOBPCG iterations cap */
     int max_ir;          /* iterative-refinement steps cap per solve (mixed precision) */
     int io_host;        /* 1: z/sigma/res/flags/member pointers of pseudo_grid are host memory */

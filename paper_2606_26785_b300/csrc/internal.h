@@ -33,6 +33,7 @@ struct pseudo_ctx;
 namespace pseudo {
 // trsv_tc.cu: the tensor-core solve (row panels of 128; n_pad is a multiple of 128)
 constexpr int TC_MB = 128;
+size_t trsv32_scratch_bytes(int64_t n_pad, int64_t ncols);
 int64_t tc_pack_floats(int n_pad);
 int64_t tc_diag_elems(int n_pad);
 void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, float *AL, float2 *DU, float2 *DL,
@@ -141,7 +142,7 @@ template <typename real>
 void launch_slot_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, const int *jv, int mmax,
                       const int *active, double *alpha, double *beta, int passes, cudaStream_t s);
 void launch_slot_tridiag(int S, int mmax, const double *alpha, const double *beta, int *active, int *jv, double *theta,
-                         double *svec, int *convd, double tol_q, double tol_floor, cudaStream_t s);
+                         double *svec, int *convd, double tol_q, double tol_floor, int fp32, cudaStream_t s);
 template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
                          const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,

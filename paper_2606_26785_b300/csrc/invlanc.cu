@@ -265,7 +265,8 @@ static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const 
         if (e != cudaSuccess) return cuda_err(e, "lanczos solve");
         h->stats.sv_R += 2 * (int64_t)ncnt;
         h->stats.lanczos_steps += 1;
-        launch_slot_tridiag(S, L.mmax, L.alpha, L.beta, L.active, L.jv, L.theta, L.svec, L.convd, tol_q, tol_floor, s);
+        launch_slot_tridiag(S, L.mmax, L.alpha, L.beta, L.active, L.jv, L.theta, L.svec, L.convd, tol_q, tol_floor,
+                            L.fp32 ? 1 : 0, s);
         harvest();
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "lanczos step");
     }

@@ -175,9 +175,10 @@ lanczos_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restri
 // ------------------------------------------------ tridiagonal eigen
 // Sturm count: number of eigenvalues of the k x k symmetric tridiagonal
 // (a, b) that are < x.
-__device__ int sturm_count(const double *a, const double *b, int k, double x, double pivmin) {
+template <typename real>
+__device__ int sturm_count(const real *a, const real *b, int k, real x, real pivmin) {
     int cnt = 0;
-    double d = a[0] - x;
+    real d = a[0] - x;
     if (fabs(d) < pivmin) d = -pivmin;
     if (d < 0) cnt++;
     for (int i = 1; i < k; ++i) {
@@ -188,66 +189,71 @@ __device__ int sturm_count(const double *a, const double *b, int k, double x, do
     return cnt;
 }
 
-// eigenvalue number `idx` (0 = smallest) by bisection
-__device__ double tridiag_eig(const double *a, const double *b, int k, int idx) {
-    double lo = a[0], hi = a[0], bmax = 0.0;
+// eigenvalue number `idx` (0 = smallest) by bisection to a few units of the
+// working precision
+template <typename real>
+__device__ real tridiag_eig(const real *a, const real *b, int k, int idx) {
+    constexpr bool dbl = sizeof(real) == 8;
+    const real eps = dbl ? (real)2.2e-16 : (real)1.2e-7;
+    const real tiny = dbl ? (real)2.2250738585072014e-308 : (real)1.1754944e-38;
+    real lo = a[0], hi = a[0];
     for (int i = 0; i < k; ++i) {
-        double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+        real r = (i > 0 ? fabs(b[i - 1]) : (real)0) + (i < k - 1 ? fabs(b[i]) : (real)0);
         lo = fmin(lo, a[i] - r);
         hi = fmax(hi, a[i] + r);
-        if (i < k - 1) bmax = fmax(bmax, fabs(b[i]));
     }
-    const double scale = fmax(fabs(lo), fabs(hi));
-    const double pivmin = fmax(2.2250738585072014e-308, 1e-300 * scale * scale + 2.2250738585072014e-308);
+    const real scale = fmax(fabs(lo), fabs(hi));
+    const real pivmin = fmax(tiny, (dbl ? (real)1e-300 : (real)1e-30) * scale * scale + tiny);
     for (int it = 0; it < 200; ++it) {
-        double mid = 0.5 * (lo + hi);
+        real mid = (real)0.5 * (lo + hi);
         if (mid <= lo || mid >= hi) break;
-        if (sturm_count(a, b, k, mid, pivmin) > idx) hi = mid; else lo = mid;
-        if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi))) break;
+        if (sturm_count<real>(a, b, k, mid, pivmin) > idx) hi = mid; else lo = mid;
+        if (hi - lo <= eps * fmax(fabs(lo), fabs(hi))) break;
     }
-    return 0.5 * (lo + hi);
+    return (real)0.5 * (lo + hi);
 }
 
 // Eigenvector of the tridiagonal for eigenvalue lam by two steps of inverse
 // iteration (tridiagonal LU with partial pivoting); result normalised.
-__device__ void tridiag_vec(const double *a, const double *b, int k, double lam, double *s, double *wk) {
+template <typename real>
+__device__ void tridiag_vec(const real *a, const real *b, int k, real lam, real *s, real *wk) {
     // wk layout: d (k), du (k), du2 (k), dl (k), piv as double (k)
-    double *d = wk, *du = wk + k, *du2 = wk + 2 * k, *dl = wk + 3 * k, *pv = wk + 4 * k;
-    const double tiny = 1e-300 + 1e-15 * fabs(lam);
-    for (int i = 0; i < k; ++i) { s[i] = 1.0; }
+    real *d = wk, *du = wk + k, *du2 = wk + 2 * k, *dl = wk + 3 * k, *pv = wk + 4 * k;
+    const real tiny = sizeof(real) == 8 ? (real)(1e-300 + 1e-15 * fabs(lam)) : (real)(1e-30f + 1e-6f * fabs(lam));
+    for (int i = 0; i < k; ++i) { s[i] = (real)1; }
     for (int rep = 0; rep < 2; ++rep) {
-        for (int i = 0; i < k; ++i) { d[i] = a[i] - lam; du[i] = i < k - 1 ? b[i] : 0.0; dl[i] = i < k - 1 ? b[i] : 0.0; du2[i] = 0.0; pv[i] = 0.0; }
+        for (int i = 0; i < k; ++i) { d[i] = a[i] - lam; du[i] = i < k - 1 ? b[i] : (real)0; dl[i] = i < k - 1 ? b[i] : (real)0; du2[i] = 0; pv[i] = 0; }
         for (int i = 0; i < k - 1; ++i) {
             if (fabs(d[i]) >= fabs(dl[i])) {
                 if (fabs(d[i]) < tiny) d[i] = tiny;
-                double f = dl[i] / d[i];
+                real f = dl[i] / d[i];
                 dl[i] = f;
                 d[i + 1] -= f * du[i];
-                pv[i] = 0.0;
+                pv[i] = 0;
             } else {
-                double f = d[i] / dl[i];
+                real f = d[i] / dl[i];
                 d[i] = dl[i];
                 dl[i] = f;
-                double tmp = du[i];
+                real tmp = du[i];
                 du[i] = d[i + 1];
                 d[i + 1] = tmp - f * d[i + 1];
                 if (i < k - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
-                pv[i] = 1.0;
+                pv[i] = 1;
             }
         }
         if (fabs(d[k - 1]) < tiny) d[k - 1] = tiny;
         // forward: apply L^{-1} P
         for (int i = 0; i < k - 1; ++i) {
-            if (pv[i] != 0.0) { double t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - dl[i] * s[i]; }
+            if (pv[i] != (real)0) { real t = s[i]; s[i] = s[i + 1]; s[i + 1] = t - dl[i] * s[i]; }
             else s[i + 1] -= dl[i] * s[i];
         }
         // backward: U^{-1}
         s[k - 1] /= d[k - 1];
         if (k > 1) s[k - 2] = (s[k - 2] - du[k - 2] * s[k - 1]) / d[k - 2];
         for (int i = k - 3; i >= 0; --i) s[i] = (s[i] - du[i] * s[i + 1] - du2[i] * s[i + 2]) / d[i];
-        double nr = 0.0;
+        real nr = 0;
         for (int i = 0; i < k; ++i) nr += s[i] * s[i];
-        nr = 1.0 / sqrt(nr);
+        nr = (real)1 / sqrt(nr);
         for (int i = 0; i < k; ++i) s[i] *= nr;
     }
 }
@@ -263,9 +269,9 @@ __global__ void lanczos_tridiag_kernel(int S, int j, int mmax, const double *__r
     const int k = j + 1;
     double a[LANCZOS_MMAX], b[LANCZOS_MMAX], s[LANCZOS_MMAX], wk[5 * LANCZOS_MMAX];
     for (int i = 0; i < k; ++i) { a[i] = alpha[(int64_t)c * mmax + i]; b[i] = beta[(int64_t)c * mmax + i]; }
-    const double th1 = tridiag_eig(a, b, k, k - 1);
-    const double th2 = k > 1 ? tridiag_eig(a, b, k, k - 2) : 0.0;
-    tridiag_vec(a, b, k, th1, s, wk);
+    const double th1 = tridiag_eig<double>(a, b, k, k - 1);
+    const double th2 = k > 1 ? tridiag_eig<double>(a, b, k, k - 2) : 0.0;
+    tridiag_vec<double>(a, b, k, th1, s, wk);
     const double rb = fabs(b[k - 1] * s[k - 1]);  // ||N^{-1} u - theta u||
     const double gap = fmax(th1 - th2, 1e-300);
     const double est = rb * rb / (th1 * gap);     // relative error bound on theta
@@ -495,6 +501,10 @@ slot_orth_kernel(cx_t<real> *__restrict__ Q, int64_t qs, cx_t<real> *__restrict_
 
 // Ritz value after step jv[c]; on convergence (or at the step cap) the slot
 // is marked finished (active = 2), otherwise its step advances.
+// The tridiagonal work runs in the precision of the recurrence: FP32 in mixed
+// mode (the returned sigma there comes from the refined Rayleigh quotient, the
+// Ritz value only steers), FP64 otherwise.
+template <typename real>
 __global__ void slot_tridiag_kernel(int S, int mmax, const double *__restrict__ alpha, const double *__restrict__ beta,
                                     int *__restrict__ active, int *__restrict__ jv, double *__restrict__ theta,
                                     double *__restrict__ svec, int *__restrict__ convd, double tol_q,
@@ -502,18 +512,18 @@ __global__ void slot_tridiag_kernel(int S, int mmax, const double *__restrict__ 
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= S || active[c] != 1) return;
     const int j = jv[c], k = j + 1;
-    double a[LANCZOS_MMAX], b[LANCZOS_MMAX], s[LANCZOS_MMAX], wk[5 * LANCZOS_MMAX];
-    for (int i = 0; i < k; ++i) { a[i] = alpha[(int64_t)c * mmax + i]; b[i] = beta[(int64_t)c * mmax + i]; }
-    const double th1 = tridiag_eig(a, b, k, k - 1);
-    const double th2 = k > 1 ? tridiag_eig(a, b, k, k - 2) : 0.0;
-    tridiag_vec(a, b, k, th1, s, wk);
-    const double rb = fabs(b[k - 1] * s[k - 1]);
-    const double gap = fmax(th1 - th2, 1e-300);
-    const double est = rb * rb / (th1 * gap);
-    const bool breakdown = b[k - 1] <= 1e-300 * th1;
-    const bool conv = breakdown || est <= tol_q || rb <= tol_floor * th1;
-    theta[c] = th1;
-    for (int i = 0; i < k; ++i) svec[(int64_t)c * mmax + i] = s[i];
+    real a[LANCZOS_MMAX], b[LANCZOS_MMAX], s[LANCZOS_MMAX], wk[5 * LANCZOS_MMAX];
+    for (int i = 0; i < k; ++i) { a[i] = (real)alpha[(int64_t)c * mmax + i]; b[i] = (real)beta[(int64_t)c * mmax + i]; }
+    const real th1 = tridiag_eig<real>(a, b, k, k - 1);
+    const real th2 = k > 1 ? tridiag_eig<real>(a, b, k, k - 2) : (real)0;
+    tridiag_vec<real>(a, b, k, th1, s, wk);
+    const double rb = fabs((double)b[k - 1] * (double)s[k - 1]);
+    const double gap = fmax((double)th1 - (double)th2, 1e-300);
+    const double est = rb * rb / ((double)th1 * gap);
+    const bool breakdown = (double)b[k - 1] <= 1e-300 * (double)th1;
+    const bool conv = breakdown || est <= tol_q || rb <= tol_floor * (double)th1;
+    theta[c] = (double)th1;
+    for (int i = 0; i < k; ++i) svec[(int64_t)c * mmax + i] = (double)s[i];
     if (conv || k == mmax) {
         active[c] = 2;
         convd[c] = conv ? 1 : 0;
@@ -650,9 +660,14 @@ void launch_slot_orth(cx_t<real> *Q, int64_t qs, cx_t<real> *W, int n, int S, co
                                                                                  passes);
 }
 void launch_slot_tridiag(int S, int mmax, const double *alpha, const double *beta, int *active, int *jv, double *theta,
-                         double *svec, int *convd, double tol_q, double tol_floor, cudaStream_t s) {
-    note_launch(); slot_tridiag_kernel<<<(S + 63) / 64, 64, 0, s>>>(S, mmax, alpha, beta, active, jv, theta, svec, convd, tol_q,
-                                                                  tol_floor);
+                         double *svec, int *convd, double tol_q, double tol_floor, int fp32, cudaStream_t s) {
+    note_launch();
+    if (fp32)
+        slot_tridiag_kernel<float><<<(S + 63) / 64, 64, 0, s>>>(S, mmax, alpha, beta, active, jv, theta, svec, convd,
+                                                               tol_q, tol_floor);
+    else
+        slot_tridiag_kernel<double><<<(S + 63) / 64, 64, 0, s>>>(S, mmax, alpha, beta, active, jv, theta, svec, convd,
+                                                                tol_q, tol_floor);
 }
 template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,

@@ -238,9 +238,9 @@ constexpr int R64 = 8, R32 = 16, NW_SOLVE = 8;
 int trsv_group_width(int fp32) { return fp32 ? R32 : R64; }
 
 size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols) {
-    int R = fp32 ? R32 : R64;
-    int64_t groups = (ncols + R - 1) / R;
-    return (size_t)groups * n_pad * R * (fp32 ? sizeof(float2) : sizeof(double2));
+    if (fp32) return trsv32_scratch_bytes(n_pad, ncols);  // shared with the tensor-core solve
+    int64_t groups = (ncols + R64 - 1) / R64;
+    return (size_t)groups * n_pad * R64 * sizeof(double2);
 }
 
 cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,

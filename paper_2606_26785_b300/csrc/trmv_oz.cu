@@ -362,12 +362,13 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                 for (int h = 0; h < OZ_NC / 16; ++h) {
                     float d[16];
                     tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + L * OZ_NC + h * 16, d);
-                    if (L < 3) {
+                    if (L < 5) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) two_sum_acc(hi[h * 16 + u], lo[h * 16 + u], d[u] * sc);
                     } else {
-                        // levels 3..6 sit below 2^-38 of the leading part: a plain
-                        // FP32 sum into the low word keeps them to 2^-62
+                        // a level-L segment sum is below 2^(9 - 8L) of the scale, so
+                        // levels 5 and 6 (< 2^-31) can go into the low word with a
+                        // plain FP32 add (rounding < 2^-55); levels up to 4 cannot
 #pragma unroll
                         for (int u = 0; u < 16; ++u) lo[h * 16 + u] = fmaf(d[u], sc, lo[h * 16 + u]);
                     }

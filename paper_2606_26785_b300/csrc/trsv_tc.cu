@@ -33,7 +33,6 @@ constexpr int KC = 16;                // complex K per chunk
 constexpr int KR = 2 * KC;            // real K per chunk
 constexpr int A_SPLIT = MB * KR;      // floats of one split of an A chunk
 constexpr int A_CHUNK = 2 * A_SPLIT;  // hi + lo
-constexpr int NTH = 128;
 
 __host__ __device__ __forceinline__ int64_t chunk_base(int64_t p) { return 4 * p * (p - 1); }
 }  // namespace
@@ -106,38 +105,91 @@ void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, 
     note_launch(); pack_tc_d_kernel<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(T, ldT, n, n_pad, DU, DL);
 }
 
+// Warp roles of the solve (256 threads):
+//   warp 0      : producer     - per chunk, one bulk copy of the packed A''
+//                                chunk and one of the B'' image of the solved
+//                                rows it multiplies, into a ring of NS stages
+//                                (chunks of the panel just solved wait for it);
+//   warp 1      : MMA issuer   - for every chunk, 12 tcgen05.mma into the
+//                                panel's TMEM accumulator (two accumulators,
+//                                so the next panel starts while the current
+//                                one is being solved);
+//   warps 4-7   : diagonal     - read the accumulator (one row per thread), form
+//                                b - D, solve the shifted 128 x 128 diagonal
+//                                block, write the rows out and the B'' images
+//                                (TF32 hi/lo, MMA byte order) of the new rows.
+// Hand-offs are mbarriers; every wait is bounded and gives up on a shared
+// abort flag.  Warps 2-3 only take part in set-up and tear-down.
+namespace {
+constexpr int NS = 4, TC_THREADS = 256;
+constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+// bounded wait that also gives up as soon as another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = tc::global_ns();
+    for (;;) {
+        if (tc::mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+        if (tc::global_ns() - t0 > 1000000000ull) { *abort = 1; return false; }
+    }
+}
+}  // namespace
+
 template <int NC>
 struct TcSmem {
     static constexpr int NR = 2 * NC;            // real N of the MMA
     static constexpr int B_SPLIT = NR * KR;      // floats
-    static constexpr size_t a_bytes = 2 * A_CHUNK * sizeof(float);
-    static constexpr size_t b_bytes = 2 * 2 * B_SPLIT * sizeof(float);
-    static constexpr size_t bytes = a_bytes + b_bytes + 128;  // + alignment slack
-    static constexpr uint32_t tmem_cols = NR < 32 ? 32 : NR;
+    static constexpr int B_IMG = 2 * B_SPLIT;    // hi + lo
+    static constexpr size_t stage = (size_t)(A_CHUNK + B_IMG) * sizeof(float);
+    static constexpr size_t bytes = NS * stage + 128;  // + alignment slack
+    static constexpr uint32_t tmem_cols = 2 * NR < 32 ? 32 : 2 * NR;  // two accumulators
 };
 
+// Scratch of the solves for ncols columns in groups of 16: the compact copy of
+// each group's solution (the CUDA-core kernel) followed by the B'' images of
+// every 16-row chunk of each group (the tensor-core kernel).
+size_t trsv32_scratch_bytes(int64_t n_pad, int64_t ncols) {
+    const int64_t groups = (ncols + 15) / 16;
+    return (size_t)groups * n_pad * 16 * sizeof(float2) +
+           (size_t)groups * (n_pad / KC) * TcSmem<16>::B_IMG * sizeof(float);
+}
+
 template <int NC>
-__global__ void __launch_bounds__(NTH)
+__global__ void __launch_bounds__(TC_THREADS, 1)
 trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
                const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err) {
     using L = TcSmem<NC>;
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
+    static_assert(NR == 32, "the diagonal warps read one 32-column accumulator");
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
+    __shared__ __align__(8) uint64_t full[NS], freeb[NS];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_free[2], solved;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
+    __shared__ int s_flag_diag;
     __shared__ int s_col[NC];
     __shared__ float2 s_z[NC];
     __shared__ float2 s_x[2][NC];
+    __shared__ int s_last_ld, s_last_mma;
 
     const int ncols = ncols_dev ? *ncols_dev : ncols_host;
     const int g = blockIdx.x;
     if (g * NC >= ncols) return;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    float *sA = reinterpret_cast<float *>(smem_raw + ((128 - (tc::smem_u32(smem_raw) & 127)) & 127));
-    float *sB = sA + 2 * A_CHUNK;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *sbuf = reinterpret_cast<float *>(smem_raw + ((128 - (tc::smem_u32(smem_raw) & 127)) & 127));
+    constexpr int STAGE_F = A_CHUNK + L::B_IMG;  // floats per stage: A'' hi, A'' lo, B'' hi, B'' lo
+    // B'' images of this group: one per 16-row chunk, after every group's compact copy
+    float *bimg = reinterpret_cast<float *>(xs_all + (int64_t)gridDim.x * n_pad * NC) +
+                  (int64_t)g * (n_pad / KC) * L::B_IMG;
 
     if (tid < NC) {
         const int pos = g * NC + tid;
@@ -149,12 +201,13 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
         s_z[tid] = make_float2((float)z.x, (float)z.y);
     }
     if (tid == 0) {
-        tc::mbar_init(&bar_ld[0], 1);
-        tc::mbar_init(&bar_ld[1], 1);
-        tc::mbar_init(&bar_mma[0], 1);
-        tc::mbar_init(&bar_mma[1], 1);
+        for (int i = 0; i < NS; ++i) { tc::mbar_init(&full[i], 1); tc::mbar_init(&freeb[i], 1); }
+        for (int i = 0; i < 2; ++i) { tc::mbar_init(&acc_full[i], 1); tc::mbar_init(&acc_free[i], 1); }
+        tc::mbar_init(&solved, 1);
         tc::mbar_fence_init();
         s_abort = 0;
+        s_last_ld = -1;
+        s_last_mma = -1;
     }
     if (warp == 0) {
         tc::tmem_alloc(&s_tmem, L::tmem_cols);
@@ -164,142 +217,160 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t sA0 = tc::smem_u32(sA), sB0 = tc::smem_u32(sB);
-    constexpr uint32_t idesc = tc::idesc_tf32(MB, NR);
-    float2 *xs = xs_all + (int64_t)g * n_pad * NC;
     const int P = n_pad / MB;
-    uint32_t q = 0;          // chunks issued so far
-    int ld_pending = -1;     // chunk whose A load thread 0 has not yet waited for
 
-    for (int p = 0; p < P; ++p) {
-        const int J = lower ? p : P - 1 - p;
-        const int nch = 8 * p;
-        const float *Ap = Apack + chunk_base(p) * A_CHUNK;
-        for (int t = 0; t < nch; ++t, ++q) {
-            const int st = q & 1;
-            if (tid == 0 && !s_abort) {
-                if (q >= 2 && !tc::mbar_wait(&bar_mma[st], ((q >> 1) - 1) & 1)) {
-                    s_abort = 1;
-                } else {
-                    tc::mbar_expect_tx(&bar_ld[st], A_CHUNK * sizeof(float));
-                    tc::bulk_g2s(sA + st * A_CHUNK, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &bar_ld[st]);
-                    ld_pending = (int)q;
-                }
-            }
-            __syncthreads();
-            if (s_abort) break;
-            {   // B'' of this chunk from the solved rows k0 .. k0 + KC - 1
-                const int k0 = lower ? KC * t : n_pad - KC * (t + 1);
-                constexpr int CPT = NC / 8;  // columns per thread (16 rows x 8 threads)
-                const int kl = tid >> 3, cb = (tid & 7) * CPT;
-                float *bh = sB + st * 2 * L::B_SPLIT, *bl = bh + L::B_SPLIT;
-                const float2 *src = xs + (int64_t)(k0 + kl) * NC + cb;
-#pragma unroll
-                for (int u = 0; u < CPT; ++u) {
-                    const float2 x = src[u];
-                    const int c = cb + u;
-                    const float v[4] = {x.x, -x.y, x.y, x.x};
-                    const int jj[4] = {c, c, NC + c, NC + c};
-                    const int kk[4] = {kl, KC + kl, kl, KC + kl};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float h = tc::to_tf32(v[e]);
-                        const int o = tc::cm_index(jj[e], kk[e], NR);
-                        bh[o] = h;
-                        bl[o] = tc::to_tf32(v[e] - h);
+    if (warp == 0) {
+        // -------------------------------------------------------- producer
+        if (lane == 0) {
+            int q = 0, known = 0;  // panels known to be solved
+            for (int p = 0; p < P && !s_abort; ++p) {
+                const float *Ap = Apack + chunk_base(p) * A_CHUNK;
+                bool ok = true;
+                for (int t = 0; t < 8 * p; ++t, ++q) {
+                    const int st = q % NS;
+                    const int k0 = lower ? KC * t : n_pad - KC * (t + 1);
+                    const int pk = lower ? k0 / MB : P - 1 - k0 / MB;  // processing index of those rows' panel
+                    if (pk >= known) {
+                        if (!wait_or_abort(&solved, pk & 1, &s_abort)) { ok = false; break; }
+                        known = pk + 1;
                     }
+                    if (q >= NS && !wait_or_abort(&freeb[st], ((q / NS) - 1) & 1, &s_abort)) { ok = false; break; }
+                    float *dst = sbuf + st * STAGE_F;
+                    tc::mbar_expect_tx(&full[st], (uint32_t)L::stage);
+                    tc::bulk_g2s(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st]);
+                    tc::bulk_g2s(dst + A_CHUNK, bimg + (int64_t)(k0 / KC) * L::B_IMG, L::B_IMG * sizeof(float),
+                                 &full[st]);
+                    s_last_ld = q;
                 }
-                tc::fence_async_smem();
+                if (!ok) break;
             }
-            __syncthreads();
-            if (tid == 0) {
-                if (!tc::mbar_wait(&bar_ld[st], (q >> 1) & 1)) {
-                    s_abort = 1;
-                } else {
-                    ld_pending = -1;
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_tf32(MB, NR);
+            const uint32_t s0 = tc::smem_u32(sbuf);
+            int q = 0;
+            for (int p = 0; p < P && !s_abort; ++p) {
+                const int buf = p & 1;
+                if (p >= 2 && !wait_or_abort(&acc_free[buf], ((p >> 1) - 1) & 1, &s_abort)) break;
+                tc::tc_fence_after();
+                const uint32_t dacc = tmem + buf * NR;
+                const int nch = 8 * p;
+                bool ok = true;
+                for (int t = 0; t < nch; ++t, ++q) {
+                    const int st = q % NS;
+                    if (!wait_or_abort(&full[st], (q / NS) & 1, &s_abort)) { ok = false; break; }
                     tc::tc_fence_after();
-                    const uint32_t ah = sA0 + st * (A_CHUNK * 4), al = ah + A_SPLIT * 4;
-                    const uint32_t bh = sB0 + st * (2 * L::B_SPLIT * 4), bl = bh + L::B_SPLIT * 4;
+                    const uint32_t ah = s0 + st * (STAGE_F * 4), al = ah + A_SPLIT * 4;
+                    const uint32_t bh = ah + A_CHUNK * 4, bl = bh + L::B_SPLIT * 4;
 #pragma unroll
                     for (int ks = 0; ks < KR / 8; ++ks) {
                         const uint64_t dah = tc::smem_desc(ah + ks * 2 * LBO_A, LBO_A, 128);
                         const uint64_t dal = tc::smem_desc(al + ks * 2 * LBO_A, LBO_A, 128);
                         const uint64_t dbh = tc::smem_desc(bh + ks * 2 * LBO_B, LBO_B, 128);
                         const uint64_t dbl = tc::smem_desc(bl + ks * 2 * LBO_B, LBO_B, 128);
-                        tc::mma_tf32(tmem, dah, dbh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-                        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
-                        tc::mma_tf32(tmem, dal, dbh, idesc, 1u);
+                        tc::mma_tf32(dacc, dah, dbh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
+                        tc::mma_tf32(dacc, dah, dbl, idesc, 1u);
+                        tc::mma_tf32(dacc, dal, dbh, idesc, 1u);
                     }
-                    tc::mma_commit(&bar_mma[st]);
+                    tc::mma_commit(&freeb[st]);
+                    s_last_mma = q;
                 }
+                if (!ok) break;
+                if (nch > 0) tc::mma_commit(&acc_full[buf]);
+                else mbar_arrive(&acc_full[buf]);
             }
         }
-        // ---- epilogue: r = b - D, then the shifted diagonal block
-        if (tid == 0 && nch > 0 && !s_abort) {
-            const uint32_t ql = q - 1;
-            if (!tc::mbar_wait(&bar_mma[ql & 1], (ql >> 1) & 1)) s_abort = 1;
-        }
-        __syncthreads();
-        if (s_abort) break;
-        tc::tc_fence_after();
-        float d[32];
-        if (nch > 0) {
-            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), d);
-        } else {
+    } else if (warp >= 4) {
+        // ------------------------------------------------------ diagonal solve
+        const int i = tid - 128, dw = warp - 4;   // row of the panel; TMEM lane quarter
+        const int kl = i % KC;
+        for (int p = 0; p < P; ++p) {
+            const int J = lower ? p : P - 1 - p;
+            const int buf = p & 1;
+            if (i == 0) s_flag_diag = wait_or_abort(&acc_full[buf], (p >> 1) & 1, &s_abort) ? 1 : 0;
+            named_bar(BAR_DIAG, 128);
+            if (!s_flag_diag) break;
+            tc::tc_fence_after();
+            float d[32];
+            if (p > 0) {
+                tc::tmem_ld32(tmem + buf * NR + ((uint32_t)(dw * 32) << 16), d);
+            } else {
 #pragma unroll
-            for (int u = 0; u < 32; ++u) d[u] = 0.f;
-        }
-        const int i = tid, row = J * MB + i;
-        const float2 *DJ = Dblk + (int64_t)J * MB * MB;
-        float2 r[NC], dinv[NC];
-        const float2 tii = DJ[i * MB + i];
+                for (int u = 0; u < 32; ++u) d[u] = 0.f;
+            }
+            tc::tc_fence_before();
+            named_bar(BAR_DIAG, 128);
+            if (i == 0) mbar_arrive(&acc_free[buf]);
+            const int row = J * MB + i;
+            const float2 *DJ = Dblk + (int64_t)J * MB * MB;
+            float2 r[NC], dinv[NC];
+            const float2 tii = DJ[i * MB + i];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            float2 b = make_float2(0.f, 0.f);
-            if (row < n && s_col[c] >= 0) b = X[(int64_t)row * ldx + s_col[c]];
-            r[c] = make_float2(b.x - d[c], b.y - d[NC + c]);
-            dinv[c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
-        }
-        if (!lower) {
-            for (int j = MB - 1; j >= 0; --j) {
-                if (i == j) {
+            for (int c = 0; c < NC; ++c) {
+                float2 b = make_float2(0.f, 0.f);
+                if (row < n && s_col[c] >= 0) b = X[(int64_t)row * ldx + s_col[c]];
+                r[c] = make_float2(b.x - d[c], b.y - d[NC + c]);
+                dinv[c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+            }
+            if (!lower) {
+                for (int j = MB - 1; j >= 0; --j) {
+                    if (i == j) {
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
+                        for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
+                    }
+                    named_bar(BAR_DIAG, 128);
+                    if (i < j) {
+                        const float2 tij = DJ[j * MB + i];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                    }
                 }
-                __syncthreads();
-                if (i < j) {
-                    const float2 tij = DJ[j * MB + i];
+            } else {
+                for (int j = 0; j < MB; ++j) {
+                    if (i == j) {
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                        for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
+                    }
+                    named_bar(BAR_DIAG, 128);
+                    if (i > j) {
+                        const float2 tij = DJ[j * MB + i];
+#pragma unroll
+                        for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                    }
                 }
             }
-        } else {
-            for (int j = 0; j < MB; ++j) {
-                if (i == j) {
+            // the rows out, and their B'' = [[Re x, Im x], [-Im x, Re x]] image
+            // (hi and lo TF32 splits) for the chunks of later panels
+            float *bh = bimg + (int64_t)(row / KC) * L::B_IMG, *bl = bh + L::B_SPLIT;
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
-                }
-                __syncthreads();
-                if (i > j) {
-                    const float2 tij = DJ[j * MB + i];
+            for (int c = 0; c < NC; ++c) {
+                const float2 v = row < n ? r[c] : make_float2(0.f, 0.f);
+                if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
+                const float vv[4] = {v.x, -v.y, v.y, v.x};
+                const int jj[4] = {c, c, NC + c, NC + c};
+                const int kk[4] = {kl, KC + kl, kl, KC + kl};
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                for (int e = 0; e < 4; ++e) {
+                    const float h = tc::to_tf32(vv[e]);
+                    const int o = tc::cm_index(jj[e], kk[e], NR);
+                    bh[o] = h;
+                    bl[o] = tc::to_tf32(vv[e] - h);
                 }
             }
+            tc::fence_async_global();
+            __threadfence_block();
+            named_bar(BAR_DIAG, 128);
+            if (i == 0) mbar_arrive(&solved);
         }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const float2 v = row < n ? r[c] : make_float2(0.f, 0.f);
-            xs[(int64_t)row * NC + c] = v;
-            if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
-        }
-        tc::tc_fence_before();
-        __syncthreads();
     }
     // ---- teardown (also after an abort: let copies and MMAs in flight finish)
+    __syncthreads();
     if (tid == 0 && s_abort) {
-        if (ld_pending >= 0) tc::mbar_wait(&bar_ld[ld_pending & 1], (ld_pending >> 1) & 1, 100000000ull);
-        if (q > 0) tc::mbar_wait(&bar_mma[(q - 1) & 1], ((q - 1) >> 1) & 1, 100000000ull);
+        const int ql = s_last_ld, qm = s_last_mma;
+        if (ql >= 0) tc::mbar_wait(&full[ql % NS], (ql / NS) & 1, 100000000ull);
+        if (qm >= 0) tc::mbar_wait(&freeb[qm % NS], (qm / NS) & 1, 100000000ull);
         atomicExch(err, 1);
     }
     tc::tc_fence_before();
@@ -322,7 +393,7 @@ cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, cons
     const int grid = (ncols + NC_TC - 1) / NC_TC;
     if (grid == 0) return cudaSuccess;
     note_launch();
-    trsv_tc_kernel<NC_TC><<<grid, NTH, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
+    trsv_tc_kernel<NC_TC><<<grid, TC_THREADS, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
                                                       h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs,
                                                       h->dev_err);
     return cudaGetLastError();
