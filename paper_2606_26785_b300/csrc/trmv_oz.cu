@@ -36,13 +36,15 @@ constexpr int OZ_NS = 7;                 // slices per operand, levels 0..6
 constexpr int OZ_CR = 64;                // complex rows per tile
 constexpr int OZ_MR = 2 * OZ_CR;         // real rows (MMA M)
 constexpr int OZ_NC = 64;                // complex columns per tile (MMA N)
-constexpr int OZ_KC = 16;                // complex K per chunk
-constexpr int OZ_KR = 2 * OZ_KC;         // real K per chunk (2 MMA k-steps)
-constexpr int OZ_SEG = 4;                // chunks per exact segment (128 real terms)
+constexpr int OZ_KC = 8;                 // complex K per chunk
+constexpr int OZ_KR = 2 * OZ_KC;         // real K per chunk (one MMA k-step of 16)
+constexpr int OZ_SEG = 128 / OZ_KR;      // chunks per exact segment (128 real terms)
+constexpr int OZ_NSTG = 4;               // ring of chunk stages in shared memory
+constexpr int OZ_TPC = 64 / OZ_KC;       // chunks per 64 complex columns
 constexpr int OZ_A_SLICE = OZ_MR * OZ_KR;            // bf16 elements
 constexpr int OZ_B_SLICE = OZ_NC * OZ_KR;
-constexpr int OZ_A_IMG = OZ_NS * OZ_A_SLICE;         // 28672 elements, 56 KB
-constexpr int OZ_B_IMG = OZ_NS * OZ_B_SLICE;         // 14336 elements, 28 KB
+constexpr int OZ_A_IMG = OZ_NS * OZ_A_SLICE;         // 14336 elements, 28 KB
+constexpr int OZ_B_IMG = OZ_NS * OZ_B_SLICE;         // 7168 elements, 14 KB
 constexpr int OZ_TH = 128;
 
 // element index of (row, k) in a bf16 core-matrix tile with R rows
@@ -53,12 +55,12 @@ __host__ __device__ __forceinline__ int64_t nchunks(int n_pad) { return n_pad / 
 // chunk range of row tile I: upper product uses complex columns >= 64 I,
 // the lower (T^H) product columns < 64 I + 64
 __host__ __device__ __forceinline__ void chunk_range(int I, int n_pad, int lower, int &c0, int &c1) {
-    if (!lower) { c0 = 4 * I; c1 = (int)nchunks(n_pad); }
-    else { c0 = 0; c1 = 4 * I + 4; }
+    if (!lower) { c0 = OZ_TPC * I; c1 = (int)nchunks(n_pad); }
+    else { c0 = 0; c1 = OZ_TPC * (I + 1); }
 }
 // first image of row tile I in the packed A slices
 __host__ __device__ __forceinline__ int64_t a_tile_base(int64_t I, int64_t n_pad, int lower) {
-    return lower ? 2 * I * (I + 1) : I * nchunks((int)n_pad) - 2 * I * (I - 1);
+    return lower ? (OZ_TPC / 2) * I * (I + 1) : I * nchunks((int)n_pad) - (OZ_TPC / 2) * I * (I - 1);
 }
 
 // alpha_s of v (|v| < 1) by repeated rounding of the exact remainder kept as
@@ -121,7 +123,7 @@ __global__ void oz_pack_a_kernel(const double2 *__restrict__ T, int64_t ldT, int
     const int64_t img = e / OZ_A_IMG;
     const int w = (int)(e % OZ_A_IMG);
     const int s = w / OZ_A_SLICE, ww = w % OZ_A_SLICE;
-    // invert cm16 for R = 128 rows, K = 32
+    // invert cm16 for R = 128 rows
     const int cmi = ww >> 6, r7 = (ww >> 3) & 7, k7 = ww & 7;
     const int kb = cmi / (OZ_MR / 8), rb = cmi % (OZ_MR / 8);
     const int r = rb * 8 + r7, kk = kb * 8 + k7;
@@ -194,36 +196,46 @@ __global__ void oz_colexp_kernel(const double2 *__restrict__ X, int n, int64_t l
     }
 }
 
-// B'' slice images: one thread per (column tile, chunk, column j, complex k)
+// B'' slice images: one thread per (column tile, chunk, column j, group of 8
+// real K entries), so that every slice is written as one 16-byte core-matrix
+// row (8 consecutive bf16) and a warp reads 32 consecutive columns of X.
 __global__ void oz_slice_b_kernel(const double2 *__restrict__ X, int n, int n_pad, int64_t ldx,
                                   const int *__restrict__ cols, int ncols, const int *__restrict__ fx,
                                   __nv_bfloat16 *__restrict__ img) {
     const int64_t NCH = nchunks(n_pad);
     const int64_t tiles = (ncols + OZ_NC - 1) / OZ_NC;
-    const int64_t total = tiles * NCH * OZ_NC * OZ_KC;
+    constexpr int KG = OZ_KR / 8;  // groups of 8 real K entries: real parts first, then imaginary parts
+    const int64_t total = tiles * NCH * OZ_NC * KG;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(w % OZ_NC);
-        const int kl = (int)((w / OZ_NC) % OZ_KC);
-        const int64_t tc_ = w / ((int64_t)OZ_KC * OZ_NC);  // tile * NCH + chunk
+        const int kg = (int)((w / OZ_NC) % KG);
+        const int64_t tc_ = w / ((int64_t)OZ_NC * KG);  // tile * NCH + chunk
         const int64_t ct = tc_ / NCH, ch = tc_ % NCH;
         const int p = (int)(ct * OZ_NC + j);
-        const int k = (int)(ch * OZ_KC + kl);
-        double2 v = make_double2(0.0, 0.0);
-        int f = 0;
-        if (p < ncols && k < n) {
-            v = X[(int64_t)k * ldx + (cols ? cols[p] : p)];
-            f = fx[p];
-        }
-        __nv_bfloat16 *base = img + tc_ * OZ_B_IMG;
+        const int part = kg / (KG / 2), kb = (kg % (KG / 2)) * 8;
+        const bool live = p < ncols;
+        const int c = live ? (cols ? cols[p] : p) : 0;
+        const int f = live ? fx[p] : 0;
+        float a[8][OZ_NS];
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            const double sv = ldexp(part ? v.y : v.x, -f);
+        for (int e = 0; e < 8; ++e) {
+            const int k = (int)(ch * OZ_KC) + kb + e;
+            double v = 0.0;
+            if (live && k < n) {
+                const double2 x = X[(int64_t)k * ldx + c];
+                v = part ? x.y : x.x;
+            }
+            const double sv = ldexp(v, -f);
             const float ph = (float)sv, pl = (float)(sv - (double)ph);
-            float a[OZ_NS];
-            slices7(ph, pl, a);
-            const int o = cm16(j, part * OZ_KC + kl, OZ_NC);
+            slices7(ph, pl, a[e]);
+        }
+        __nv_bfloat16 *base = img + tc_ * OZ_B_IMG + cm16(j, kg * 8, OZ_NC);
 #pragma unroll
-            for (int s = 0; s < OZ_NS; ++s) base[s * OZ_B_SLICE + o] = __float2bfloat16_rn(a[s]);
+        for (int s = 0; s < OZ_NS; ++s) {
+            __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(a[e][s]);
+            *reinterpret_cast<uint4 *>(base + s * OZ_B_SLICE) = *reinterpret_cast<const uint4 *>(h);
         }
     }
 }
@@ -251,8 +263,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 }
 
 struct OzSmem {
-    static constexpr size_t stage = (size_t)(OZ_A_IMG + OZ_B_IMG) * sizeof(__nv_bfloat16);  // 84 KB
-    static constexpr size_t bytes = 2 * stage + 128;
+    static constexpr size_t stage = (size_t)(OZ_A_IMG + OZ_B_IMG) * sizeof(__nv_bfloat16);  // 42 KB
+    static constexpr size_t bytes = OZ_NSTG * stage + 128;
 };
 
 __global__ void __launch_bounds__(OZ_TH, 1)
@@ -262,7 +274,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                const double2 *__restrict__ B, int64_t ldb, double2 *__restrict__ Y, int64_t ldy, int subtract,
                int *err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar_ld[2], bar_mma[2];
+    __shared__ __align__(8) uint64_t bar_ld[OZ_NSTG], bar_mma[OZ_NSTG];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -279,10 +291,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     const __nv_bfloat16 *Bp = Bimg + ((int64_t)ct * NCH + c0) * OZ_B_IMG;
 
     if (tid == 0) {
-        tc::mbar_init(&bar_ld[0], 1);
-        tc::mbar_init(&bar_ld[1], 1);
-        tc::mbar_init(&bar_mma[0], 1);
-        tc::mbar_init(&bar_mma[1], 1);
+        for (int i = 0; i < OZ_NSTG; ++i) { tc::mbar_init(&bar_ld[i], 1); tc::mbar_init(&bar_mma[i], 1); }
         tc::mbar_fence_init();
         s_abort = 0;
     }
@@ -304,21 +313,23 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     for (int j = 0; j < OZ_NC; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
 
     auto issue_load = [&](int q) {
-        const int st = q & 1;
+        const int st = q % OZ_NSTG;
         tc::mbar_expect_tx(&bar_ld[st], (uint32_t)OzSmem::stage);
         unsigned char *dst = base + st * OzSmem::stage;
         tc::bulk_g2s(dst, Ap + (int64_t)q * OZ_A_IMG, OZ_A_IMG * 2, &bar_ld[st]);
         tc::bulk_g2s(dst + OZ_A_IMG * 2, Bp + (int64_t)q * OZ_B_IMG, OZ_B_IMG * 2, &bar_ld[st]);
     };
     int ld_pending = -1, mma_last = -1;
-    if (tid == 0 && nch > 0) { issue_load(0); ld_pending = 0; }
+    // chunks 0 .. NSTG-2 in flight before the first MMA; chunk q + NSTG - 1 is
+    // loaded into the stage of chunk q - 1 once its MMAs are done
+    if (tid == 0)
+        for (int q = 0; q < OZ_NSTG - 1 && q < nch; ++q) { issue_load(q); ld_pending = q; }
     for (int q = 0; q < nch; ++q) {
-        const int st = q & 1;
+        const int st = q % OZ_NSTG;
         if (tid == 0 && !s_abort) {
-            if (!tc::mbar_wait(&bar_ld[st], (q >> 1) & 1)) {
+            if (!tc::mbar_wait(&bar_ld[st], (q / OZ_NSTG) & 1)) {
                 s_abort = 1;
             } else {
-                ld_pending = -1;
                 tc::tc_fence_after();
                 const uint32_t a0 = s0 + st * STAGE, b0 = a0 + OZ_A_IMG * 2;
                 const bool seg_first = (q % OZ_SEG) == 0;
@@ -337,21 +348,20 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                 }
                 tc::mma_commit(&bar_mma[st]);
                 mma_last = q;
-                // the other stage held chunk q - 1: refill it with chunk q + 1
-                // once those MMAs are done (chunk q's are queued behind them)
-                if (q + 1 < nch) {
-                    if (q >= 1 && !tc::mbar_wait(&bar_mma[(q - 1) & 1], ((q - 1) >> 1) & 1)) {
+                const int qn = q + OZ_NSTG - 1;
+                if (qn < nch) {
+                    if (q >= 1 && !tc::mbar_wait(&bar_mma[(q - 1) % OZ_NSTG], ((q - 1) / OZ_NSTG) & 1)) {
                         s_abort = 1;
                     } else {
-                        issue_load(q + 1);
-                        ld_pending = q + 1;
+                        issue_load(qn);
+                        ld_pending = qn;
                     }
                 }
             }
         }
         // end of an exact segment: fold the level sums into the double-single totals
         if ((q % OZ_SEG) == OZ_SEG - 1 || q == nch - 1) {
-            if (tid == 0 && !s_abort && !tc::mbar_wait(&bar_mma[st], (q >> 1) & 1)) s_abort = 1;
+            if (tid == 0 && !s_abort && !tc::mbar_wait(&bar_mma[st], (q / OZ_NSTG) & 1)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
             tc::tc_fence_after();
@@ -406,8 +416,8 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
         }
     }
     if (tid == 0 && s_abort) {
-        if (ld_pending >= 0) tc::mbar_wait(&bar_ld[ld_pending & 1], (ld_pending >> 1) & 1, 100000000ull);
-        if (mma_last >= 0) tc::mbar_wait(&bar_mma[mma_last & 1], (mma_last >> 1) & 1, 100000000ull);
+        if (ld_pending >= 0) tc::mbar_wait(&bar_ld[ld_pending % OZ_NSTG], (ld_pending / OZ_NSTG) & 1, 100000000ull);
+        if (mma_last >= 0) tc::mbar_wait(&bar_mma[mma_last % OZ_NSTG], (mma_last / OZ_NSTG) & 1, 100000000ull);
         atomicExch(err, 1);
     }
     tc::tc_fence_before();

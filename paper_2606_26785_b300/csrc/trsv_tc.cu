@@ -314,28 +314,31 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                 r[c] = make_float2(b.x - d[c], b.y - d[NC + c]);
                 dinv[c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
             }
-            if (!lower) {
-                for (int j = MB - 1; j >= 0; --j) {
+            // The coefficient of step j is loaded PD steps ahead: a load issued
+            // after the step's barrier would expose the cache latency 128 times
+            // per panel.
+            constexpr int PD = 16;
+            float2 pf[PD];
+#pragma unroll
+            for (int u = 0; u < PD; ++u) {
+                const int j = lower ? u : MB - 1 - u;
+                pf[u] = (lower ? i > j : i < j) ? DJ[j * MB + i] : make_float2(0.f, 0.f);
+            }
+            for (int blk = 0; blk < MB / PD; ++blk) {
+#pragma unroll
+                for (int u = 0; u < PD; ++u) {
+                    const int step = blk * PD + u;
+                    const int j = lower ? step : MB - 1 - step;
+                    const float2 tij = pf[u];
+                    const int jn = lower ? j + PD : j - PD;
+                    pf[u] = (jn >= 0 && jn < MB && (lower ? i > jn : i < jn)) ? DJ[jn * MB + i]
+                                                                             : make_float2(0.f, 0.f);
                     if (i == j) {
 #pragma unroll
                         for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
                     }
                     named_bar(BAR_DIAG, 128);
-                    if (i < j) {
-                        const float2 tij = DJ[j * MB + i];
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
-                    }
-                }
-            } else {
-                for (int j = 0; j < MB; ++j) {
-                    if (i == j) {
-#pragma unroll
-                        for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
-                    }
-                    named_bar(BAR_DIAG, 128);
-                    if (i > j) {
-                        const float2 tij = DJ[j * MB + i];
+                    if (lower ? i > j : i < j) {
 #pragma unroll
                         for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
                     }
