@@ -45,7 +45,8 @@ constexpr int OZ_A_SLICE = OZ_MR * OZ_KR;            // bf16 elements
 constexpr int OZ_B_SLICE = OZ_NC * OZ_KR;
 constexpr int OZ_A_IMG = OZ_NS * OZ_A_SLICE;         // 14336 elements, 28 KB
 constexpr int OZ_B_IMG = OZ_NS * OZ_B_SLICE;         // 7168 elements, 14 KB
-constexpr int OZ_TH = 128;
+constexpr int OZ_TH = 256;  // two warpgroups: each TMEM lane quarter is read by two warps,
+                             // one per half of the output columns
 
 // element index of (row, k) in a bf16 core-matrix tile with R rows
 __host__ __device__ __forceinline__ int cm16(int row, int k, int R) {
@@ -308,9 +309,12 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     constexpr uint32_t STAGE = (uint32_t)OzSmem::stage;
     const uint32_t s0 = tc::smem_u32(base);
 
-    float hi[OZ_NC], lo[OZ_NC];
+    constexpr int HC = OZ_NC / 2;              // output columns per thread
+    const int lq = warp & 3, hc = warp >> 2;    // TMEM lane quarter, column half
+    const int rr = lq * 32 + (tid & 31);        // real row of the tile (TMEM lane)
+    float hi[HC], lo[HC];
 #pragma unroll
-    for (int j = 0; j < OZ_NC; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    for (int j = 0; j < HC; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
 
     auto issue_load = [&](int q) {
         const int st = q % OZ_NSTG;
@@ -333,18 +337,17 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                 tc::tc_fence_after();
                 const uint32_t a0 = s0 + st * STAGE, b0 = a0 + OZ_A_IMG * 2;
                 const bool seg_first = (q % OZ_SEG) == 0;
-#pragma unroll 1
-                for (int ks = 0; ks < OZ_KR / 16; ++ks) {
-#pragma unroll 1
-                    for (int L = 0; L < OZ_NS; ++L) {
-#pragma unroll 1
-                        for (int sa = 0; sa <= L; ++sa) {
-                            const int sb = L - sa;
-                            const uint64_t da = tc::smem_desc(a0 + sa * (OZ_A_SLICE * 2) + ks * 2 * LBO_A, LBO_A, 128);
-                            const uint64_t db = tc::smem_desc(b0 + sb * (OZ_B_SLICE * 2) + ks * 2 * LBO_B, LBO_B, 128);
-                            mma_bf16(tmem + L * OZ_NC, da, db, idesc, (seg_first && ks == 0 && sa == 0) ? 0u : 1u);
-                        }
-                    }
+                // one descriptor per operand stage; a slice is a fixed offset (the
+                // start-address field holds smem byte address >> 4 and cannot carry)
+                const uint64_t da0 = tc::smem_desc(a0, LBO_A, 128), db0 = tc::smem_desc(b0, LBO_B, 128);
+                constexpr uint64_t AS = (OZ_A_SLICE * 2) >> 4, BS = (OZ_B_SLICE * 2) >> 4;
+                static_assert(OZ_KR == 16, "one MMA k-step per chunk");
+#pragma unroll
+                for (int L = 0; L < OZ_NS; ++L) {
+#pragma unroll
+                    for (int sa = 0; sa <= L; ++sa)
+                        mma_bf16(tmem + L * OZ_NC, da0 + sa * AS, db0 + (L - sa) * BS, idesc,
+                                 (seg_first && sa == 0) ? 0u : 1u);
                 }
                 tc::mma_commit(&bar_mma[st]);
                 mma_last = q;
@@ -369,9 +372,9 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
             for (int L = 0; L < OZ_NS; ++L) {
                 const float sc = ldexpf(1.f, -14 - 8 * L);
 #pragma unroll
-                for (int h = 0; h < OZ_NC / 16; ++h) {
+                for (int h = 0; h < HC / 16; ++h) {
                     float d[16];
-                    tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + L * OZ_NC + h * 16, d);
+                    tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + L * OZ_NC + hc * HC + h * 16, d);
                     if (L < 5) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) two_sum_acc(hi[h * 16 + u], lo[h * 16 + u], d[u] * sc);
@@ -392,17 +395,18 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     // The stage buffers are free now; the sums go through them so that the
     // per-column loop below needs no register-resident arrays.
     if (!s_abort) {
-        double *sums = reinterpret_cast<double *>(base);  // [OZ_NC][OZ_TH]
+        double *sums = reinterpret_cast<double *>(base);  // [OZ_NC][OZ_MR]
 #pragma unroll
-        for (int j = 0; j < OZ_NC; ++j) sums[j * OZ_TH + tid] = (double)hi[j] + (double)lo[j];
-        const int part = tid / OZ_CR, i = I * OZ_CR + (tid % OZ_CR);
+        for (int j = 0; j < HC; ++j) sums[(hc * HC + j) * OZ_MR + rr] = (double)hi[j] + (double)lo[j];
+        const int part = rr / OZ_CR, i = I * OZ_CR + (rr % OZ_CR);
         if (i < n) {
             const int e_i = ex[i];
-            const int jmax = min(OZ_NC, ncols - ct * OZ_NC);
-            for (int j = 0; j < jmax; ++j) {
+            const int jmax = min(HC, ncols - ct * OZ_NC - hc * HC);
+            for (int jj = 0; jj < jmax; ++jj) {
+                const int j = hc * HC + jj;
                 const int p = ct * OZ_NC + j;
                 const int c = cols ? cols[p] : p;
-                double y = ldexp(sums[j * OZ_TH + tid], e_i + fx[p]);
+                double y = ldexp(sums[j * OZ_MR + rr], e_i + fx[p]);
                 const double2 x = X[(int64_t)i * ldx + c];
                 if (zc) {
                     const double2 z = zc[c];

@@ -121,7 +121,13 @@ void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, 
 // Hand-offs are mbarriers; every wait is bounded and gives up on a shared
 // abort flag.  Warps 2-3 only take part in set-up and tear-down.
 namespace {
-constexpr int NS = 4, TC_THREADS = 256;
+#ifndef TC_NS
+#define TC_NS 4
+#endif
+#ifndef TC_NC
+#define TC_NC 16
+#endif
+constexpr int NS = TC_NS, TC_THREADS = 256;
 constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
 
 __device__ __forceinline__ void named_bar(int id, int count) {
@@ -148,7 +154,9 @@ struct TcSmem {
     static constexpr int B_SPLIT = NR * KR;      // floats
     static constexpr int B_IMG = 2 * B_SPLIT;    // hi + lo
     static constexpr size_t stage = (size_t)(A_CHUNK + B_IMG) * sizeof(float);
-    static constexpr size_t bytes = NS * stage + 128;  // + alignment slack
+    // ring of stages, then the turned-around accumulator and 1 / (t_ii - z_c)
+    static constexpr size_t diag = (size_t)MB * (2 * NC + 1) * sizeof(float) + (size_t)MB * NC * sizeof(float2);
+    static constexpr size_t bytes = NS * stage + diag + 128;  // + alignment slack
     static constexpr uint32_t tmem_cols = 2 * NR < 32 ? 32 : 2 * NR;  // two accumulators
 };
 
@@ -156,20 +164,20 @@ struct TcSmem {
 // each group's solution (the CUDA-core kernel) followed by the B'' images of
 // every 16-row chunk of each group (the tensor-core kernel).
 size_t trsv32_scratch_bytes(int64_t n_pad, int64_t ncols) {
-    const int64_t groups = (ncols + 15) / 16;
-    return (size_t)groups * n_pad * 16 * sizeof(float2) +
-           (size_t)groups * (n_pad / KC) * TcSmem<16>::B_IMG * sizeof(float);
+    const int64_t groups = (ncols + TC_NC - 1) / TC_NC;  // TC_NC is a multiple of the CUDA-core group (16)
+    return (size_t)groups * n_pad * TC_NC * sizeof(float2) +
+           (size_t)groups * (n_pad / KC) * TcSmem<TC_NC>::B_IMG * sizeof(float);
 }
 
 template <int NC>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, TC_NS <= 2 ? 2 : 1)
 trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
                const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err) {
     using L = TcSmem<NC>;
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
-    static_assert(NR == 32, "the diagonal warps read one 32-column accumulator");
+    static_assert(NR % 32 == 0, "the diagonal warps read the accumulator in 32-column pieces");
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[NS], freeb[NS];
     __shared__ __align__(8) uint64_t acc_full[2], acc_free[2], solved;
@@ -178,7 +186,6 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
     __shared__ int s_flag_diag;
     __shared__ int s_col[NC];
     __shared__ float2 s_z[NC];
-    __shared__ float2 s_x[2][NC];
     __shared__ int s_last_ld, s_last_mma;
 
     const int ncols = ncols_dev ? *ncols_dev : ncols_host;
@@ -284,8 +291,16 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
         }
     } else if (warp >= 4) {
         // ------------------------------------------------------ diagonal solve
-        const int i = tid - 128, dw = warp - 4;   // row of the panel; TMEM lane quarter
-        const int kl = i % KC;
+        // The accumulator arrives one row per thread (TMEM lane = row); it is
+        // turned around through shared memory so that each warp owns NC/4
+        // columns of all 128 rows (rows lane + 32k, k = 0..3) and solves them
+        // on its own: one shuffle broadcast per step and no block barrier in
+        // the 128 steps.
+        constexpr int CPW = NC / 4;
+        const int i = tid - 128, dw = warp - 4;
+        const int cw0 = dw * CPW;
+        float *Dsm = sbuf + NS * STAGE_F;                 // [MB][2 NC + 1]
+        float2 *s_dinv = reinterpret_cast<float2 *>(Dsm + MB * (2 * NC + 1));  // [MB][NC]
         for (int p = 0; p < P; ++p) {
             const int J = lower ? p : P - 1 - p;
             const int buf = p & 1;
@@ -293,73 +308,101 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
             named_bar(BAR_DIAG, 128);
             if (!s_flag_diag) break;
             tc::tc_fence_after();
-            float d[32];
-            if (p > 0) {
-                tc::tmem_ld32(tmem + buf * NR + ((uint32_t)(dw * 32) << 16), d);
-            } else {
+            const float2 *DJ = Dblk + (int64_t)J * MB * MB;
+            {   // row i: accumulator into shared memory, and 1 / (t_ii - z_c)
 #pragma unroll
-                for (int u = 0; u < 32; ++u) d[u] = 0.f;
+                for (int piece = 0; piece < NR / 32; ++piece) {
+                    float d[32];
+                    if (p > 0) {
+                        tc::tmem_ld32(tmem + buf * NR + piece * 32 + ((uint32_t)(dw * 32) << 16), d);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 32; ++u) d[u] = 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) Dsm[i * (2 * NC + 1) + piece * 32 + u] = d[u];
+                }
+                const float2 tii = DJ[i * MB + i];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) s_dinv[i * NC + c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
             }
             tc::tc_fence_before();
             named_bar(BAR_DIAG, 128);
             if (i == 0) mbar_arrive(&acc_free[buf]);
-            const int row = J * MB + i;
-            const float2 *DJ = Dblk + (int64_t)J * MB * MB;
-            float2 r[NC], dinv[NC];
-            const float2 tii = DJ[i * MB + i];
+            // this warp's columns cw0 .. cw0 + CPW - 1, rows lane + 32 k
+            float2 r[4][CPW];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                float2 b = make_float2(0.f, 0.f);
-                if (row < n && s_col[c] >= 0) b = X[(int64_t)row * ldx + s_col[c]];
-                r[c] = make_float2(b.x - d[c], b.y - d[NC + c]);
-                dinv[c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+            for (int k = 0; k < 4; ++k) {
+                const int rl = lane + 32 * k, row = J * MB + rl;
+#pragma unroll
+                for (int c = 0; c < CPW; ++c) {
+                    const int col = cw0 + c;
+                    float2 b = make_float2(0.f, 0.f);
+                    if (row < n && s_col[col] >= 0) b = X[(int64_t)row * ldx + s_col[col]];
+                    r[k][c] = make_float2(b.x - Dsm[rl * (2 * NC + 1) + col], b.y - Dsm[rl * (2 * NC + 1) + NC + col]);
+                }
             }
-            // The coefficient of step j is loaded PD steps ahead: a load issued
-            // after the step's barrier would expose the cache latency 128 times
-            // per panel.
-            constexpr int PD = 16;
-            float2 pf[PD];
+            // coefficient of x_j in this thread's rows, loaded PD steps ahead
+            // (the stored blocks are zero where a row does not depend on x_j)
+            constexpr int PD = 8;
+            float2 pf[PD][4];
 #pragma unroll
             for (int u = 0; u < PD; ++u) {
                 const int j = lower ? u : MB - 1 - u;
-                pf[u] = (lower ? i > j : i < j) ? DJ[j * MB + i] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) pf[u][k] = DJ[j * MB + lane + 32 * k];
             }
-            for (int blk = 0; blk < MB / PD; ++blk) {
 #pragma unroll
-                for (int u = 0; u < PD; ++u) {
-                    const int step = blk * PD + u;
-                    const int j = lower ? step : MB - 1 - step;
-                    const float2 tij = pf[u];
-                    const int jn = lower ? j + PD : j - PD;
-                    pf[u] = (jn >= 0 && jn < MB && (lower ? i > jn : i < jn)) ? DJ[jn * MB + i]
-                                                                             : make_float2(0.f, 0.f);
-                    if (i == j) {
+            for (int kq = 0; kq < 4; ++kq) {              // the 32-row slot of the step's row
+                const int kj = lower ? kq : 3 - kq;
+                for (int blk = 0; blk < 32 / PD; ++blk) {
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) { r[c] = cmul(r[c], dinv[c]); s_x[j & 1][c] = r[c]; }
-                    }
-                    named_bar(BAR_DIAG, 128);
-                    if (lower ? i > j : i < j) {
+                    for (int u = 0; u < PD; ++u) {
+                        const int lj = lower ? blk * PD + u : 31 - (blk * PD + u);
+                        const int j = 32 * kj + lj;
+                        float2 t[4];
 #pragma unroll
-                        for (int c = 0; c < NC; ++c) cfms(r[c], tij, s_x[j & 1][c]);
+                        for (int k = 0; k < 4; ++k) t[k] = pf[u][k];
+                        const int jn = lower ? j + PD : j - PD;
+                        if (jn >= 0 && jn < MB) {
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) pf[u][k] = DJ[jn * MB + lane + 32 * k];
+                        }
+                        // x_j for this warp's columns: computed from lane lj's row, broadcast
+#pragma unroll
+                        for (int c = 0; c < CPW; ++c) {
+                            const float2 xo = cmul(r[kj][c], s_dinv[j * NC + cw0 + c]);
+                            const float2 xb = shfl_c(xo, lj);
+                            if (lane == lj) r[kj][c] = xb;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (k != kj || lane != lj) cfms(r[k][c], t[k], xb);
+                        }
                     }
                 }
             }
             // the rows out, and their B'' = [[Re x, Im x], [-Im x, Re x]] image
             // (hi and lo TF32 splits) for the chunks of later panels
-            float *bh = bimg + (int64_t)(row / KC) * L::B_IMG, *bl = bh + L::B_SPLIT;
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const float2 v = row < n ? r[c] : make_float2(0.f, 0.f);
-                if (row < n && s_col[c] >= 0) X[(int64_t)row * ldx + s_col[c]] = v;
-                const float vv[4] = {v.x, -v.y, v.y, v.x};
-                const int jj[4] = {c, c, NC + c, NC + c};
-                const int kk[4] = {kl, KC + kl, kl, KC + kl};
+            for (int k = 0; k < 4; ++k) {
+                const int rl = lane + 32 * k, row = J * MB + rl;
+                const int kl = rl % KC;
+                float *bh = bimg + (int64_t)(row / KC) * L::B_IMG, *bl = bh + L::B_SPLIT;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float h = tc::to_tf32(vv[e]);
-                    const int o = tc::cm_index(jj[e], kk[e], NR);
-                    bh[o] = h;
-                    bl[o] = tc::to_tf32(vv[e] - h);
+                for (int c = 0; c < CPW; ++c) {
+                    const int col = cw0 + c;
+                    const float2 v = row < n ? r[k][c] : make_float2(0.f, 0.f);
+                    if (row < n && s_col[col] >= 0) X[(int64_t)row * ldx + s_col[col]] = v;
+                    const float vv[4] = {v.x, -v.y, v.y, v.x};
+                    const int jj[4] = {col, col, NC + col, NC + col};
+                    const int kk[4] = {kl, KC + kl, kl, KC + kl};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float h = tc::to_tf32(vv[e]);
+                        const int o = tc::cm_index(jj[e], kk[e], NR);
+                        bh[o] = h;
+                        bl[o] = tc::to_tf32(vv[e] - h);
+                    }
                 }
             }
             tc::fence_async_global();
@@ -382,7 +425,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
     if (warp == 0) tc::tmem_dealloc(tmem, L::tmem_cols);
 }
 
-constexpr int NC_TC = 16;
+constexpr int NC_TC = TC_NC;
 int trsv_tc_group_width() { return NC_TC; }
 
 cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
@@ -404,8 +447,8 @@ cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, cons
 
 cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                     const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
-    // both kernels take 16 columns per CTA, so they share one scratch size
-    static_assert(NC_TC == 16, "scratch of the tensor-core solve is sized like the CUDA-core one");
+    // the scratch (trsv32_scratch_bytes) covers both kernels' column groups
+    static_assert(NC_TC % 16 == 0, "tensor-core column groups are whole CUDA-core groups");
     if (h->fp32_solver == 0 && h->tcA_U)
         return launch_trsv_tc(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
