@@ -137,6 +137,7 @@ struct RecyLayout {
     double2 *U, *Y, *NX, *X64, *R64, *B64, *zc;
     float2 *D32;
     float2 *xh, *xl;  // FP32 split of a product operand, n x max(B, lanes * k_max)
+    void *oz;         // tensor-core product scratch (mixed precision), max(B, lanes * r) columns
     int *need, *perm, *mask;  // refinement plan of the polish
     double *rn2, *s2, *rr;
     // update (slots up to L)
@@ -218,6 +219,7 @@ static void recy_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     R.D32 = c.get<float2>(n * B);
     R.xh = c.get<float2>(n * std::max<size_t>(B, R.Ld));
     R.xl = c.get<float2>(n * std::max<size_t>(B, R.Ld));
+    R.oz = R.fp32 ? c.take(oz_scratch_bytes(h->n_pad, std::max<int64_t>(B, (int64_t)L * r))) : nullptr;
     R.need = c.get<int>(B);
     R.perm = c.get<int>(B);
     R.mask = c.get<int>(B);
@@ -304,7 +306,7 @@ static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int poli
     const int n = h->n;
     cudaError_t e = cudaSuccess;
     if (polish) {
-        IRBufs ib{R.R64, R.D32, R.rn2, R.mask, R.need, R.perm, (float2 *)R.xs, R.xh, R.xl, nullptr};
+        IRBufs ib{R.R64, R.D32, R.rn2, R.mask, R.need, R.perm, (float2 *)R.xs, R.xh, R.xl, R.oz};
         IRPlan plan;
         {
             std::vector<double> xi((size_t)R.B * LB_MAXM), sg(cnt);
@@ -326,8 +328,8 @@ static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int poli
         cudaMemcpyAsync(R.U, R.X64, (size_t)n * cnt * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
     int k1 = kp_begin(h, s);
-    trmv_hp(h, R.fp32, 0, nullptr, R.zc, cnt, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s, R.xh, R.xl);
-    trmv_hp(h, R.fp32, 1, nullptr, R.zc, cnt, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s, R.xh, R.xl);
+    trmv_hp(h, R.fp32, 0, nullptr, R.zc, cnt, R.U, cnt, nullptr, cnt, R.Y, cnt, 0, s, R.xh, R.xl, R.oz);
+    trmv_hp(h, R.fp32, 1, nullptr, R.zc, cnt, R.Y, cnt, nullptr, cnt, R.NX, cnt, 0, s, R.xh, R.xl, R.oz);
     kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 2 * tri_flops(n, cnt), 2 * tri_bytes(n, cnt, 16, 16, 2), s);
     h->stats.mv_M_fp64_refine += 2 * (int64_t)cnt;
     launch_rq_residual(R.U, R.Y, R.NX, n, cnt, nullptr, R.s2, R.rr, s);
@@ -537,9 +539,9 @@ static int update_slot(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, const
     // W1+ = T V+, W4+ = T^H V+, W3+ = T^H W1+  (3r products with M per update)
     note_launch(); lane_cols_kernel<<<(nu * r + 127) / 128, 128, 0, s>>>(R.slot_lanes, R.kk, nu, r, KM, R.ucols);
     const int k1 = kp_begin(h, s);
-    trmv_hp(h, R.fp32, 0, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s, R.xh, R.xl);
-    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s, R.xh, R.xl);
-    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s, R.xh, R.xl);
+    trmv_hp(h, R.fp32, 0, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W1, Ld, 0, s, R.xh, R.xl, R.oz);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.V, Ld, nullptr, Ld, R.W4, Ld, 0, s, R.xh, R.xl, R.oz);
+    trmv_hp(h, R.fp32, 1, R.ucols, nullptr, nu * r, R.W1, Ld, nullptr, Ld, R.W3, Ld, 0, s, R.xh, R.xl, R.oz);
     kp_end(h, k1, R.fp32 ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64, 3 * tri_flops(n, nu * r),
            3 * tri_bytes(n, nu * r, 16, 16, 2), s);
     h->stats.mv_M += 3 * (int64_t)nu * r;
