@@ -342,10 +342,12 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                 const uint64_t da0 = tc::smem_desc(a0, LBO_A, 128), db0 = tc::smem_desc(b0, LBO_B, 128);
                 constexpr uint64_t AS = (OZ_A_SLICE * 2) >> 4, BS = (OZ_B_SLICE * 2) >> 4;
                 static_assert(OZ_KR == 16, "one MMA k-step per chunk");
+                // A slice outer, level inner: consecutive MMAs go to different
+                // level accumulators and do not wait on each other
 #pragma unroll
-                for (int L = 0; L < OZ_NS; ++L) {
+                for (int sa = 0; sa < OZ_NS; ++sa) {
 #pragma unroll
-                    for (int sa = 0; sa <= L; ++sa)
+                    for (int L = sa; L < OZ_NS; ++L)
                         mma_bf16(tmem + L * OZ_NC, da0 + sa * AS, db0 + (L - sa) * BS, idesc,
                                  (seg_first && sa == 0) ? 0u : 1u);
                 }

@@ -127,6 +127,12 @@ namespace {
 #ifndef TC_NC
 #define TC_NC 16
 #endif
+#ifndef TC_NACC
+#define TC_NACC 6   // independent accumulators per panel (MMAs into one accumulator serialise)
+#endif
+#ifndef TC_PD
+#define TC_PD 8   // prefetch distance of the diagonal-block coefficients (steps)
+#endif
 constexpr int NS = TC_NS, TC_THREADS = 256;
 constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
 
@@ -157,7 +163,10 @@ struct TcSmem {
     // ring of stages, then the turned-around accumulator and 1 / (t_ii - z_c)
     static constexpr size_t diag = (size_t)MB * (2 * NC + 1) * sizeof(float) + (size_t)MB * NC * sizeof(float2);
     static constexpr size_t bytes = NS * stage + diag + 128;  // + alignment slack
-    static constexpr uint32_t tmem_cols = 2 * NR < 32 ? 32 : 2 * NR;  // two accumulators
+    // two panels in flight, TC_NACC partial accumulators each (power of two >= 32 columns)
+    static constexpr uint32_t acc_cols = 2 * TC_NACC * NR;
+    static constexpr uint32_t tmem_cols = acc_cols <= 32 ? 32 : acc_cols <= 64 ? 64 : acc_cols <= 128 ? 128
+                                          : acc_cols <= 256 ? 256 : 512;
 };
 
 // Scratch of the solves for ncols columns in groups of 16: the compact copy of
@@ -262,7 +271,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                 const int buf = p & 1;
                 if (p >= 2 && !wait_or_abort(&acc_free[buf], ((p >> 1) - 1) & 1, &s_abort)) break;
                 tc::tc_fence_after();
-                const uint32_t dacc = tmem + buf * NR;
+                const uint32_t dacc = tmem + buf * (TC_NACC * NR);
                 const int nch = 8 * p;
                 bool ok = true;
                 for (int t = 0; t < nch; ++t, ++q) {
@@ -277,9 +286,13 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                         const uint64_t dal = tc::smem_desc(al + ks * 2 * LBO_A, LBO_A, 128);
                         const uint64_t dbh = tc::smem_desc(bh + ks * 2 * LBO_B, LBO_B, 128);
                         const uint64_t dbl = tc::smem_desc(bl + ks * 2 * LBO_B, LBO_B, 128);
-                        tc::mma_tf32(dacc, dah, dbh, idesc, (t > 0 || ks > 0) ? 1u : 0u);
-                        tc::mma_tf32(dacc, dah, dbl, idesc, 1u);
-                        tc::mma_tf32(dacc, dal, dbh, idesc, 1u);
+                        // consecutive MMAs go to different partial accumulators so that
+                        // they do not wait on each other; the diagonal warps add them up
+                        constexpr int NA = TC_NACC;
+                        const int g3 = (3 * ks) % NA;
+                        tc::mma_tf32(dacc + ((g3 + 0) % NA) * NR, dah, dbh, idesc, (t == 0 && 3 * ks + 0 < NA) ? 0u : 1u);
+                        tc::mma_tf32(dacc + ((g3 + 1) % NA) * NR, dah, dbl, idesc, (t == 0 && 3 * ks + 1 < NA) ? 0u : 1u);
+                        tc::mma_tf32(dacc + ((g3 + 2) % NA) * NR, dal, dbh, idesc, (t == 0 && 3 * ks + 2 < NA) ? 0u : 1u);
                     }
                     tc::mma_commit(&freeb[st]);
                     s_last_mma = q;
@@ -313,11 +326,19 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
 #pragma unroll
                 for (int piece = 0; piece < NR / 32; ++piece) {
                     float d[32];
-                    if (p > 0) {
-                        tc::tmem_ld32(tmem + buf * NR + piece * 32 + ((uint32_t)(dw * 32) << 16), d);
-                    } else {
 #pragma unroll
-                        for (int u = 0; u < 32; ++u) d[u] = 0.f;
+                    for (int u = 0; u < 32; ++u) d[u] = 0.f;
+                    if (p > 0) {
+                        // panels with fewer than TC_NACC MMAs leave the later
+                        // accumulators unwritten: only the ones in use are read
+                        const int used = min(TC_NACC, 8 * p * 3 * (KR / 8));
+                        for (int a = 0; a < used; ++a) {
+                            float e[32];
+                            tc::tmem_ld32(tmem + buf * (TC_NACC * NR) + a * NR + piece * 32 +
+                                          ((uint32_t)(dw * 32) << 16), e);
+#pragma unroll
+                            for (int u = 0; u < 32; ++u) d[u] += e[u];
+                        }
                     }
 #pragma unroll
                     for (int u = 0; u < 32; ++u) Dsm[i * (2 * NC + 1) + piece * 32 + u] = d[u];
@@ -344,7 +365,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
             }
             // coefficient of x_j in this thread's rows, loaded PD steps ahead
             // (the stored blocks are zero where a row does not depend on x_j)
-            constexpr int PD = 8;
+            constexpr int PD = TC_PD;
             float2 pf[PD][4];
 #pragma unroll
             for (int u = 0; u < PD; ++u) {
