@@ -137,7 +137,7 @@ struct RecyLayout {
     double2 *U, *Y, *NX, *X64, *R64, *B64, *zc;
     float2 *D32;
     float2 *xh, *xl;  // FP32 split of a product operand, n x max(B, lanes * k_max)
-    void *oz;         // tensor-core product scratch (mixed precision), max(B, lanes * r) columns
+    void *oz;         // tensor-core product scratch (unused: see recycle_carve)
     int *need, *perm, *mask;  // refinement plan of the polish
     double *rn2, *s2, *rr;
     // update (slots up to L)
@@ -219,7 +219,11 @@ static void recy_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     R.D32 = c.get<float2>(n * B);
     R.xh = c.get<float2>(n * std::max<size_t>(B, R.Ld));
     R.xl = c.get<float2>(n * std::max<size_t>(B, R.Ld));
-    R.oz = R.fp32 ? c.take(oz_scratch_bytes(h->n_pad, std::max<int64_t>(B, (int64_t)L * r))) : nullptr;
+    // The recycling path keeps the CUDA-core double-single products: it has no
+    // FP64 fallback, and near-singular points (sigma far below ||T|| ||x||) need
+    // the element-wise accuracy of double-single, which the column-scaled
+    // tensor-core slicing does not give for strongly graded vectors.
+    R.oz = nullptr;
     R.need = c.get<int>(B);
     R.perm = c.get<int>(B);
     R.mask = c.get<int>(B);

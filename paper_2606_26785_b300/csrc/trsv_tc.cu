@@ -122,16 +122,16 @@ void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, 
 // abort flag.  Warps 2-3 only take part in set-up and tear-down.
 namespace {
 #ifndef TC_NS
-#define TC_NS 4
+#define TC_NS 2   // 2 stages: two CTAs fit on an SM (shared memory, 128 registers)
 #endif
 #ifndef TC_NC
 #define TC_NC 16
 #endif
 #ifndef TC_NACC
-#define TC_NACC 6   // independent accumulators per panel (MMAs into one accumulator serialise)
+#define TC_NACC 1   // partial accumulators per panel (more did not pay off when measured)
 #endif
 #ifndef TC_PD
-#define TC_PD 8   // prefetch distance of the diagonal-block coefficients (steps)
+#define TC_PD 4   // prefetch distance of the diagonal-block coefficients (steps)
 #endif
 constexpr int NS = TC_NS, TC_THREADS = 256;
 constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
