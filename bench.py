@@ -22,6 +22,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -115,7 +116,7 @@ def _nominal_fp32_tflops(peaks):
     return 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
 
 
-FP64_MEASURED_TFLOPS = 1.13  # DFMA probe on this machine's B300
+FP64_MEASURED_TFLOPS = 1.13  # B300 FP64 FMA rate measured with independent DFMA chains on all SMs
 
 
 def _tf32x3_tflops(peaks):
@@ -144,6 +145,15 @@ def roofline(kst, peaks, tensor_solve=True):
                 "peak_source": "measured cuBLAS bf16 sustained x 1.1/2.25 (TF32/bf16 nominal) / 3 (3xTF32)"}
     if name in ("trsv32",):
         peak, unit, bound = fp32, "TFLOP/s", "alu"
+    elif name == "trmv_ds" and tensor_solve:
+        # the double-single-accurate product on the tensor cores: 28 bf16 slice
+        # products stand in for one real product
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1800.0) * 0.78)) / 28.0
+        return {"kernel": "trmv_ds (tcgen05 bf16 slices)", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "launches": k["launches"],
+                "avg_launch_ms": per_launch_ms, "algorithmic_flops_per_launch": flops, "share_of_step": None,
+                "peak_source": "measured cuBLAS bf16 sustained / 28 (slice pairs per real product)"}
     elif name == "trmv_ds":
         # double-single: 12 FP32 operations per real multiply-add (2 algorithmic flops)
         peak, unit, bound = fp32 / 6.0, "TFLOP/s", "alu"
@@ -186,6 +196,9 @@ def main():
                     help="method timed as the main line (the other one is reported under comparisons)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison paths and the CPU baseline")
+    ap.add_argument("--profile-kernel", choices=["solve", "product"],
+                    help="for kernel profilers: 3 warm-up calls then 1 timed call of the tensor-core solve or the "
+                         "tensor-core double-single-accurate product on 4096 columns of the bench matrix")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: mixed inverse Lanczos on 4096 grid points, one untimed run")
     args = ap.parse_args()
@@ -207,6 +220,30 @@ def main():
         dist.init_process_group("nccl")
     W, t_schur = make_workload()
     h = p.Pseudo(W.T)
+    if args.profile_kernel:
+        rng = np.random.default_rng(0)
+        ncols = 4096
+        X0 = torch.from_numpy(rng.standard_normal((W.n, ncols)) + 1j * rng.standard_normal((W.n, ncols))).cuda()
+        zk = torch.from_numpy(W.z[::9][:ncols].copy()).cuda()
+
+        def call():
+            if args.profile_kernel == "solve":
+                X = X0.clone()
+                h.solve(X, zk, adjoint=False, precision=p.MIXED)
+            else:
+                h.matvec(X0, z=zk, precision=p.MIXED)
+
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_kernel": args.profile_kernel, "columns": ncols, "workload": WORKLOAD,
+                          "ms_incl_conversions": e0.elapsed_time(e1)}))
+        return
     if args.profile_case:
         zs = torch.from_numpy(W.z[::9][:4096].copy()).cuda()
         o = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8, maxiter_lanczos=32)
@@ -237,8 +274,7 @@ def main():
     torch.cuda.synchronize()
     h.reset_stats()
     times = []
-    out_dir = ROOT / "gpurun_out"
-    clocks = Clocks(str(out_dir / "bench_clocks.csv") if out_dir.exists() else "/tmp/bench_clocks.csv")
+    clocks = Clocks(os.environ.get("PSEUDO_BENCH_CLOCKS_CSV", os.path.join(tempfile.gettempdir(), "bench_clocks.csv")))
     lc0 = p._abi.load().pseudo_launch_count()
     with clocks:
         for _ in range(args.steps):
