@@ -239,6 +239,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
         // -------------------------------------------------------- producer
         if (lane == 0) {
             int q = 0, known = 0;  // panels known to be solved
+            const uint64_t keep = tc::l2_policy_evict_last();  // every CTA streams the same A chunks
             for (int p = 0; p < P && !s_abort; ++p) {
                 const float *Ap = Apack + chunk_base(p) * A_CHUNK;
                 bool ok = true;
@@ -253,7 +254,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                     if (q >= NS && !wait_or_abort(&freeb[st], ((q / NS) - 1) & 1, &s_abort)) { ok = false; break; }
                     float *dst = sbuf + st * STAGE_F;
                     tc::mbar_expect_tx(&full[st], (uint32_t)L::stage);
-                    tc::bulk_g2s(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st]);
+                    tc::bulk_g2s_hint(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st], keep);
                     tc::bulk_g2s(dst + A_CHUNK, bimg + (int64_t)(k0 / KC) * L::B_IMG, L::B_IMG * sizeof(float),
                                  &full[st]);
                     s_last_ld = q;
