@@ -116,6 +116,7 @@ def _nominal_fp32_tflops(peaks):
     return 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
 
 
+N_BENCH = 2000
 FP64_MEASURED_TFLOPS = 1.13  # B300 FP64 FMA rate measured with independent DFMA chains on all SMs
 
 
@@ -126,6 +127,14 @@ def _tf32x3_tflops(peaks):
     FP32 product."""
     bf16 = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1800.0) * 0.78))
     return bf16 * (1.1 / 2.25) / 3.0
+
+
+# DRAM bytes (read + write) per column of a launch, from one ncu capture of each
+# tensor-core kernel on 4,096 columns of the bench matrix (bench.py
+# --profile-kernel solve|product; profiles/trsv_tc_kernel_gaussian2000.md and
+# profiles/trmv_oz_kernel_gaussian2000.md); traffic grows with the columns of a
+# launch (A re-reads per column tile, B images per column group).
+DRAM_BYTES_PER_COLUMN = {"trsv32": (1.694567e9 + 0.3204608e9) / 4096, "trmv_ds": (1.939070e9 + 0.111231e9) / 4096}
 
 
 def roofline(kst, peaks, tensor_solve=True):
@@ -139,8 +148,11 @@ def roofline(kst, peaks, tensor_solve=True):
     if name == "trsv32" and tensor_solve:
         achieved = flops / (per_launch_ms / 1e3) / 1e12
         peak = _tf32x3_tflops(peaks)
+        cols = flops / (4.0 * N_BENCH * N_BENCH)
         return {"kernel": "trsv32 (tcgen05 3xTF32)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "launches": k["launches"],
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": DRAM_BYTES_PER_COLUMN["trsv32"] * cols, "traffic_unit": "bytes per launch (ncu, scaled)",
+                "launches": k["launches"],
                 "avg_launch_ms": per_launch_ms, "algorithmic_flops_per_launch": flops, "share_of_step": None,
                 "peak_source": "measured cuBLAS bf16 sustained x 1.1/2.25 (TF32/bf16 nominal) / 3 (3xTF32)"}
     if name in ("trsv32",):
@@ -150,8 +162,11 @@ def roofline(kst, peaks, tensor_solve=True):
         # products stand in for one real product
         achieved = flops / (per_launch_ms / 1e3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1800.0) * 0.78)) / 28.0
+        cols = flops / (4.0 * N_BENCH * N_BENCH)
         return {"kernel": "trmv_ds (tcgen05 bf16 slices)", "bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "launches": k["launches"],
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": DRAM_BYTES_PER_COLUMN["trmv_ds"] * cols, "traffic_unit": "bytes per launch (ncu, scaled)",
+                "launches": k["launches"],
                 "avg_launch_ms": per_launch_ms, "algorithmic_flops_per_launch": flops, "share_of_step": None,
                 "peak_source": "measured cuBLAS bf16 sustained / 28 (slice pairs per real product)"}
     elif name == "trmv_ds":
