@@ -131,9 +131,8 @@ def _tf32x3_tflops(peaks):
 
 # DRAM bytes (read + write) per column of a launch, from one ncu capture of each
 # tensor-core kernel on 4,096 columns of the bench matrix (bench.py
-# --profile-kernel solve|product; profiles/trsv_tc_kernel_gaussian2000.md and
-# profiles/trmv_oz_kernel_gaussian2000.md); traffic grows with the columns of a
-# launch (A re-reads per column tile, B images per column group).
+# --profile-kernel solve|product); traffic grows with the columns of a launch
+# (A re-reads per column tile, B images per column group).
 DRAM_BYTES_PER_COLUMN = {"trsv32": (1.694567e9 + 0.3204608e9) / 4096, "trmv_ds": (1.939070e9 + 0.111231e9) / 4096}
 
 
