@@ -60,3 +60,32 @@ def test_triangular8000_mixed_matches_fp64():
     err = np.abs(a - b)
     assert np.all(err[ok] <= 1e-8 * a[ok] + 4 * 8000 * 2.2e-16 * fro), float((err[ok] / a[ok]).max())
     h.close()
+
+
+@pytest.mark.parametrize("mode,k", [("recycle", 8), ("recycle", 32), ("invlanc", 0)])
+def test_toeplitz1200_mixed(mode, k):
+    """The banded Toeplitz + noise workload, reduced to n = 1200 on a 50 x 50
+    grid over the full-size window, in mixed precision: the recycling path with
+    recycled rank k (r = 4, p_max = k / 4) and the inverse-Lanczos path, against
+    stored oracle values (tests/golden/toeplitz1200_samples.json, written by
+    tests/golden/make_toeplitz_samples.py)."""
+    import paper_2606_26785_b300 as p
+
+    g = json.loads((GOLD / "toeplitz1200_samples.json").read_text())
+    C = workloads.toeplitz_noisy(g["n"], 5)
+    T, _, err = workloads.schur(C)
+    z = workloads.grid(-1.5, 1.5, -1.0, 1.0, g["nx"], g["ny"])
+    idx = np.array(g["index"])
+    assert np.allclose(z[idx], np.array([complex(a, b) for a, b in g["z"]]))
+    h = p.Pseudo(T)
+    if mode == "recycle":
+        out = h.grid(z, workloads.EPS_LEVELS, mode=p.RECYCLE, precision=p.MIXED, rtol=1e-8, r=4, p_max=k // 4,
+                     grid_nx=g["nx"], grid_ny=g["ny"], batch_b=20)
+    else:
+        out = h.grid(z, workloads.EPS_LEVELS, mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
+    sig = out["sigma"].cpu().numpy()[idx]
+    rep = check_sigma(sig, np.array(g["sigma_ref"]), n=g["n"], fro=g["fro_norm"], schur_err=err,
+                      oracle_off=np.array(g["oracle_off"]), rtol=1e-8)
+    print(mode, k, rep, h.stats())
+    assert rep["n_included"] > 0 and rep["n_bad"] == 0, rep
+    h.close()
