@@ -256,7 +256,7 @@ int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pse
  *   X, z, ncols, adjoint, stream : as for pseudo_solve (X device, in place; z device).
  * Scratch: a fixed 16 MiB array inside the library (2^20 complex doubles), held
  * by every GPU that loads the library until the process exits.  The solve needs
- * ceil(ncols / 8) * n_pad * 8 of its elements (n_pad = n rounded up to 64), so
+ * ceil(ncols / 8) * n_pad * 8 of its elements (n_pad = n rounded up to 128), so
  * n = 2000 allows up to 512 columns per call; larger calls return
  * PSEUDO_ERR_ARG with a message and launch nothing.
  * The first call on a device looks up the array's device address (with the

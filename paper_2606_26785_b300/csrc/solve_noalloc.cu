@@ -3,12 +3,13 @@
 // library-usage entry point.
 //
 // The solve needs scratch memory (a compact copy of the solved columns, one
-// 64-row-padded n x 8 block per group of 8 columns).  pseudo_solve takes it
-// from a caller-provided workspace; this entry point uses a fixed array in the
-// library's own device memory instead, so a caller with no allocator at all
-// (a process that reserved its whole device-memory budget up front, or a
-// latency-critical loop that must not call cudaMalloc/cudaFree because they
-// can synchronise the device) can still run solves.
+// n_pad x 8 block per group of 8 columns, n_pad = n rounded up to 128).
+// pseudo_solve takes it from a caller-provided workspace; this entry point
+// uses a fixed array in the library's own device memory instead, so a caller
+// with no allocator at all (a process that reserved its whole device-memory
+// budget up front, or a latency-critical loop that must not call
+// cudaMalloc/cudaFree because they can synchronise the device) can still run
+// solves.
 #include <mutex>
 
 #include "common.cuh"
