@@ -414,7 +414,11 @@ static int lobpcg_refine(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, int
     copy_item_blocks(R, n, R.CSn, 0, R.CS, 0, nact, s);
     int np = 0;  // columns in P
     const double rt = o->rtol > 0.0 ? o->rtol : 0.0;
-    const double rtol_lob = R.fp32 ? 0.0 : rt;  // mixed: paper test, then FP64 polish
+    // both precisions stop LOBPCG on the Kato--Temple-style estimate: the
+    // refinement step after it improves the vector but cannot separate a
+    // cluster of nearly equal singular values, so a point whose gap is too
+    // small for the accuracy target must end flagged as not converged
+    const double rtol_lob = rt;
     int it = 0;
     for (it = 0; it < o->maxiter_lobpcg && nact > 0; ++it) {
         // W = C^H (C X) - X Xi^2
