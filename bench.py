@@ -5,13 +5,18 @@ workload (n = 2000, entries N(0, 1/n) in real and imaginary parts, seed 2;
 timed), with the accuracy of the timed run checked against stored oracle
 values (rel err <= 1e-8 under the pass rule of tests/parity.py).
 
-One step = one pseudo_grid call over all 40,000 points with the recycled
-Rayleigh--Ritz-SVD path (k = 16, r = 4) in mixed precision.  The timed
-region is bracketed by barriers + device synchronisation; L2 is flushed
-(256 MB write) between timed steps.  Also reported: the plain FP64 inverse-
-Lanczos path and the mixed inverse-Lanczos path on a bounded sample of the
-same grid, the end-to-end number through the host-buffer C-ABI call, the
-roofline of the dominant kernel and the CPU oracle on a bounded sample.
+One step = one pseudo_grid call over all 40,000 points with the shift-
+batched inverse Lanczos path in mixed precision (tensor-core solves and
+double-single-accurate refinement residuals, FP64 fallback for the points
+that need it).  The timed region is bracketed by barriers + device
+synchronisation; L2 is flushed (256 MB write) between timed steps.  Also
+reported: the end-to-end number through the host-buffer C-ABI call, the
+roofline of the dominant kernel from per-kernel CUDA-event times, the
+recycled Rayleigh--Ritz-SVD path (k = 16, r = 4; mixed and FP64) on the full
+grid, the plain FP64 inverse Lanczos (shift-batched and per point) on
+samples of the grid, and the CPU oracle on a bounded sample.  Under torchrun
+every rank runs its own copy of the workload (independent replicas, weak
+scaling); the step time is the maximum over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -200,6 +205,24 @@ def cpu_baseline(W, budget_points=1):
                       f"C - zI using all {threads} host threads inside the point; {dt:.1f} s"}
 
 
+def max_over_ranks(ms, dist, device):
+    """Step time of the whole job: the slowest rank's (every rank passes its
+    own mean step time; dist is None in a single-process run)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank, world, ms):
+    """Whole-job points/s: the points all ranks processed over the job's step
+    time in milliseconds."""
+    return points_per_rank * world / (ms / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -307,15 +330,12 @@ def main():
             times.append(e0.elapsed_time(e1))
     launches = p._abi.load().pseudo_launch_count() - lc0
     ms = float(np.mean(times))
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     st = h.stats()
     sigma = out["sigma"].cpu().numpy()
     acc = check_accuracy(sigma, W)
     npts = W.z.size
-    value = npts * world / (ms / 1e3)
+    value = job_throughput(npts, world, ms)
     peaks = _peaks()
 
     # one profiled step: per-kernel CUDA-event times on the launching stream
@@ -344,13 +364,16 @@ def main():
     e2e_t = []
     for _ in range(max(1, args.steps)):
         flush.zero_()
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h.grid_host(zpin, eps, opts=hopts, workspace=e2e_ws, out=outs)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e = {"value": npts / float(np.mean(e2e_t)), "unit": "points/s", "h2d_bytes_per_step": int(npts * 16),
-           "d2h_bytes_per_step": int(npts * (8 + 8 + 4 + 4))}
+    e2e_ms = max_over_ranks(float(np.mean(e2e_t)) * 1e3, dist, "cuda")
+    e2e = {"value": job_throughput(npts, world, e2e_ms), "unit": "points/s",
+           "h2d_bytes_per_step": int(npts * 16 * world), "d2h_bytes_per_step": int(npts * (8 + 8 + 4 + 4) * world)}
 
     extras = {}
     cpu = None
