@@ -20,6 +20,9 @@ Contents
     the recycled Rayleigh--Ritz-SVD (Alg. 1) and the recycle-subspace update
     (Alg. 2) written out step by step in NumPy, used to check intermediate
     quantities of the GPU path on small cases.
+``traversal.batch_zigzag(nx, ny, b)``
+    the batch-zigzag visiting order of a Cartesian grid (Sec. 2.3, eq.
+    (batch)), pinned in ``tests/test_oracle_traversal.py``.
 
 Pins (all in ``tests/test_oracle_pins.py``, run with ``-m "not gpu"``): closed
 forms for normal matrices, n = 1 and n = 2 brute force, unitary invariance,

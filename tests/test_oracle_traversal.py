@@ -1,0 +1,61 @@
+"""The batch-zigzag traversal (Sec. 2.3, eq. (batch)): the oracle pinned by
+hand-worked grids, the special cases the definition reduces to and the
+geometry of its steps; the library's host-side order (pseudo_traversal_order,
+the one the recycling path walks) compared with it index for index."""
+import numpy as np
+import pytest
+
+from oracle.traversal import batch_zigzag
+
+# (nx, ny, b) -> visiting order worked out by hand on the grid
+# z[iy * nx + ix]; first batch row left to right, second right to left
+HAND = {
+    # 3 x 4 grid, b = 2: batches (x, rows 0-1) for x = 0, 1, 2, then
+    # (x, rows 2-3) for x = 2, 1, 0
+    (3, 4, 2): [0, 3, 1, 4, 2, 5, 8, 11, 7, 10, 6, 9],
+    # 2 x 5 grid, b = 2: the top batch row holds one point per column
+    (2, 5, 2): [0, 2, 1, 3, 5, 7, 4, 6, 8, 9],
+    # 4 x 3 grid, b = 3: one batch row, whole columns left to right
+    (4, 3, 3): [0, 4, 8, 1, 5, 9, 2, 6, 10, 3, 7, 11],
+}
+
+
+@pytest.mark.parametrize("key", sorted(HAND))
+def test_hand_worked_grids(key):
+    assert batch_zigzag(*key) == HAND[key]
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (3, 3), (5, 2), (4, 7)])
+def test_b1_is_the_row_wise_zigzag(nx, ny):
+    # b = 1: the textbook boustrophedon, even rows left to right, odd rows right to left
+    want = []
+    for iy in range(ny):
+        xs = range(nx) if iy % 2 == 0 else range(nx - 1, -1, -1)
+        want += [iy * nx + ix for ix in xs]
+    assert batch_zigzag(nx, ny, 1) == want
+
+
+@pytest.mark.parametrize("nx,ny,b", [(3, 4, 4), (5, 3, 9)])
+def test_b_at_least_ny_sweeps_whole_columns(nx, ny, b):
+    assert batch_zigzag(nx, ny, b) == [iy * nx + ix for ix in range(nx) for iy in range(ny)]
+
+
+@pytest.mark.parametrize("nx,ny,b", [(9, 9, 3), (7, 10, 3), (12, 5, 4), (1, 6, 4), (6, 1, 2)])
+def test_permutation_and_step_geometry(nx, ny, b):
+    order = batch_zigzag(nx, ny, b)
+    assert sorted(order) == list(range(nx * ny))
+    pts = [(i % nx, i // nx) for i in order]
+    for (x0, y0), (x1, y1) in zip(pts, pts[1:]):
+        if y0 // b == y1 // b and x0 == x1:  # inside a batch: one step up
+            assert y1 == y0 + 1
+        elif y0 // b == y1 // b:  # next batch of the same batch row: one column over, back to its bottom
+            assert abs(x1 - x0) == 1 and y1 == (y1 // b) * b
+            assert (x1 - x0) == (1 if (y0 // b) % 2 == 0 else -1)
+        else:  # next batch row: same column (the zigzag turn), one point up
+            assert x1 == x0 and y1 == y0 + 1 and y1 % b == 0
+
+
+def test_degenerate_grids():
+    assert batch_zigzag(0, 5, 2) == []
+    assert batch_zigzag(3, 0, 2) == []
+    assert batch_zigzag(3, 2, 0) == batch_zigzag(3, 2, 1)
