@@ -202,6 +202,25 @@ int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo_c64 *const
  * Errors: ARG. */
 int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t npts, int64_t *out);
 
+/* The order in which the recycling path (PSEUDO_RECYCLE) visits the points of
+ * a Cartesian grid: the batch-zigzag traversal of Sec. 2.3, eq. (batch).  The
+ * grid is cut into column batches of b vertically adjacent points (the top
+ * batch row is shorter when b does not divide grid_ny); batch rows are taken
+ * from the bottom, swept in a row-wise zigzag (the first left to right, the
+ * next right to left, and so on), and the points of each batch are visited
+ * bottom to top.  The recycling path splits this sequence into `lanes`
+ * contiguous segments.
+ *   npts             : number of points; must equal grid_nx * grid_ny when
+ *                      grid_nx > 0 (at most 2^31 - 1).
+ *   grid_nx, grid_ny : the layout of pseudo_opts (z[iy * grid_nx + ix]);
+ *                      grid_nx = 0 means unordered points, visited in index
+ *                      order.
+ *   batch_b          : b; values below 1 are taken as 1, as pseudo_grid does.
+ *   order            : caller-owned host array of npts int32, written with the
+ *                      point indices in visiting order.
+ * Host-only: needs no handle and no device.  Errors: ARG. */
+int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int32_t *order);
+
 /* Counters and phase timings accumulated since create or the last reset. */
 int pseudo_stats(pseudo_handle h, pseudo_stats_t *out);
 int pseudo_stats_reset(pseudo_handle h);

@@ -18,6 +18,7 @@ EXPORTED = (
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
     "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count", "pseudo_recycle_state_layout",
     "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch", "pseudo_matvec_workspace_bytes",
+    "pseudo_traversal_order",
 )
 
 

@@ -59,3 +59,24 @@ def test_degenerate_grids():
     assert batch_zigzag(0, 5, 2) == []
     assert batch_zigzag(3, 0, 2) == []
     assert batch_zigzag(3, 2, 0) == batch_zigzag(3, 2, 1)
+
+
+@pytest.mark.parametrize("nx,ny,b", [(3, 4, 2), (2, 5, 2), (9, 9, 3), (200, 200, 20), (37, 53, 7), (8, 3, 1),
+                                     (5, 4, 100), (1, 1, 1), (64, 64, 0)])
+def test_library_order_matches_oracle(nx, ny, b):
+    import paper_2606_26785_b300 as p
+
+    got = p.traversal_order(nx, ny, b)
+    assert got.dtype == np.int32
+    assert got.tolist() == batch_zigzag(nx, ny, b)
+
+
+def test_library_order_unordered_points_and_errors():
+    import paper_2606_26785_b300 as p
+
+    assert p.traversal_order(0, 0, 4, npts=6).tolist() == list(range(6))
+    assert p.traversal_order(0, 0, 4, npts=0).tolist() == []
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(3, 4, 2, npts=11)
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(-1, 4, 2, npts=4)
