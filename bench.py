@@ -19,6 +19,7 @@ every rank runs its own copy of the workload (independent replicas, weak
 scaling); the step time is the maximum over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --workload multi [--matrices M]   # many matrices through pseudo_grid_batch
 """
 from __future__ import annotations
 
@@ -238,12 +239,17 @@ def main():
                          "tensor-core double-single-accurate product on 4096 columns of the bench matrix")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: mixed inverse Lanczos on 4096 grid points, one untimed run")
+    ap.add_argument("--workload", default="gaussian2000", choices=["gaussian2000", "multi"],
+                    help="multi: the multi-matrix workload through pseudo_grid_batch (one GPU, its own JSON line)")
+    ap.add_argument("--matrices", type=int, default=16, help="with --workload multi: how many of the 64 matrices")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "multi":
+        return run_multi(args)
 
     import torch
 
@@ -445,6 +451,84 @@ def check_accuracy_rtol(sigma, W, rtol):
     idx = np.array(g["index"])
     return check_sigma(np.asarray(sigma)[idx], np.array(g["sigma_ref"]), n=W.n, fro=g["fro_norm"],
                        schur_err=W.schur_err, oracle_off=np.array(g["oracle_off"]), rtol=rtol)
+
+
+BATCH_GOLDEN = ROOT / "tests" / "golden" / "batch16_samples.json"
+
+
+def run_multi(args):
+    """The multi-matrix workload: independent complex Gaussian matrices
+    N(0, 1/n), n log-uniform in [256, 2048] (seed 40), each on its own 64 x 64
+    grid over [-1.5, 1.5]^2; the first --matrices of its sequence (host Schur
+    factors not timed).  One step = one pseudo_grid_batch call over all of
+    them in mixed precision; the same matrices one after another with
+    pseudo_grid are timed beside it.  Accuracy: the stored oracle values of
+    the 8 smallest of the first 16 matrices."""
+    import torch
+
+    import paper_2606_26785_b300 as p
+    from paper_2606_26785_b300 import workloads
+    from tests.parity import check_sigma
+
+    nm = args.matrices
+    t0 = time.time()
+    mats = workloads.gaussian_batch(64, 40)[:nm]
+    Ts, errs = [], []
+    for C in mats:
+        T, _, e = workloads.schur(C)
+        Ts.append(T)
+        errs.append(e)
+    t_prep = time.time() - t0
+    sizes = [C.shape[0] for C in mats]
+    zh = workloads.grid(-1.5, 1.5, -1.5, 1.5, 64, 64)
+    z = torch.from_numpy(zh).cuda()
+    hs = [p.Pseudo(T) for T in Ts]
+    opts = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
+    eps = (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10)
+    npts = nm * zh.size
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    for _ in range(args.warmup):
+        outs, _ = p.grid_batch(hs, [z] * nm, eps, opts=opts)
+    lc0 = p._abi.load().pseudo_launch_count()
+    t_batch = [timed(lambda: p.grid_batch(hs, [z] * nm, eps, opts=opts)) for _ in range(args.steps)]
+    launches = (p._abi.load().pseudo_launch_count() - lc0) // max(1, args.steps)
+    outs = t_batch[-1][1][0]
+    ms = float(np.mean([t for t, _ in t_batch]))
+    ms_seq = float(np.mean([timed(lambda: [h.grid(z, eps, opts=opts) for h in hs])[0]
+                            for _ in range(max(1, min(2, args.steps)))]))
+    acc = None
+    if BATCH_GOLDEN.exists():
+        g = json.loads(BATCH_GOLDEN.read_text())
+        smp = [s_ for s_ in g["samples"] if s_["matrix"] < nm]
+        m0 = min(nm, g["count"])
+        if smp and g["sizes"][:m0] == sizes[:m0]:
+            got = np.array([outs[s_["matrix"]]["sigma"][s_["index"]].item() for s_ in smp])
+            bad = 0
+            worst = 0.0
+            for v, s_ in zip(got, smp):
+                rep = check_sigma(np.array([v]), np.array([s_["sigma_ref"]]), n=s_["n"], fro=s_["fro_norm"],
+                                  schur_err=errs[s_["matrix"]], oracle_off=np.array([s_["oracle_off"]]), rtol=1e-8)
+                bad += rep["n_bad"]
+                worst = max(worst, abs(v - s_["sigma_ref"]) / s_["sigma_ref"])
+            acc = {"n_points": len(smp), "n_bad": int(bad), "max_rel_err": worst}
+    print(json.dumps({
+        "metric": METRIC, "value": npts / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64+f32",
+        "data": "synthetic", "gpu_launches": int(launches),
+        "config": {"workload": f"multi-matrix: first {nm} of 64 complex Gaussian matrices N(0,1/n), "
+                               "n log-uniform in [256,2048] (seed 40), 64x64 grid each over [-1.5,1.5]^2",
+                   "sizes": sizes, "points": npts, "host_schur_s": t_prep},
+        "sequential_pseudo_grid": {"ms": ms_seq, "points_per_s": npts / (ms_seq / 1e3)},
+        "accuracy": acc}))
 
 
 def run_reference(args, rank, world):
