@@ -3,12 +3,28 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <type_traits>
 
 namespace pseudo {
 
 // Counts every kernel launch the library makes (process-wide).
 void note_launch();
+
+// Raises a kernel's dynamic shared-memory limit before its first launch on
+// each device (the attribute is per device; `done` holds one bit per device
+// ordinal).  Host threads may race here: a thread sees a device's bit only
+// after a completed set, and a repeated set is harmless.
+template <typename Kernel>
+inline void smem_attr_once(Kernel kernel, int bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    done.fetch_or(bit, std::memory_order_release);
+}
 
 // ---------------------------------------------------------------- complex
 template <typename real> struct cx;

@@ -222,11 +222,8 @@ static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower
                                const double2 *zc, int ncols, const int *ncols_dev, cx_t<real> *X,
                                int64_t ldx, cx_t<real> *xs, cudaStream_t s) {
     size_t sm = trsv_smem<real, R, NW>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trsv_ms_kernel<real, R, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(trsv_ms_kernel<real, R, NW>, (int)sm, attr);
     int grid = (ncols + R - 1) / R;
     if (grid == 0) return cudaSuccess;
     note_launch(); trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs);

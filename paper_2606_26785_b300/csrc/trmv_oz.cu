@@ -436,11 +436,8 @@ cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, cons
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
                            int subtract, void *scratch, cudaStream_t s) {
     if (ncols <= 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trmv_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OzSmem::bytes);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(trmv_oz_kernel, (int)OzSmem::bytes, attr);
     const int n = h->n, n_pad = h->n_pad;
     char *p = (char *)(((uintptr_t)scratch + 255) & ~(uintptr_t)255);
     const int64_t tiles = (ncols + OZ_NC - 1) / OZ_NC;

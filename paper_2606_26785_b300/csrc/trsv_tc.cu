@@ -453,11 +453,8 @@ int trsv_tc_group_width() { return NC_TC; }
 cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
     using L = TcSmem<NC_TC>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trsv_tc_kernel<NC_TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(trsv_tc_kernel<NC_TC>, (int)L::bytes, attr);
     const int grid = (ncols + NC_TC - 1) / NC_TC;
     if (grid == 0) return cudaSuccess;
     note_launch();

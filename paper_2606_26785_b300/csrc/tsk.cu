@@ -82,11 +82,8 @@ cudaError_t launch_ts_gram(TSView A, int ka, TSView B, int kb, int n, int nitems
     slice = slice > TS_ROWS ? TS_ROWS : slice;
     if (slice < 1) slice = 1;
     size_t sm = sizeof(double2) * (size_t)slice * (ka + kb);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(ts_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(ts_gram_kernel, 160 * 1024, attr);
     dim3 grid(nitems, (n + slice - 1) / slice);
     note_launch(); ts_gram_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, B, kb, n, items, G, gstride, slice);
     return cudaGetLastError();
@@ -96,11 +93,8 @@ cudaError_t launch_ts_mul(TSView A, int ka, const double2 *C, int64_t cstride, T
                           const int *items, double beta, double alpha, cudaStream_t s) {
     if (nitems <= 0 || kb <= 0) return cudaSuccess;
     size_t sm = sizeof(double2) * (size_t)(ka > 0 ? ka : 1) * kb;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(ts_mul_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(ts_mul_kernel, 160 * 1024, attr);
     dim3 grid(nitems, (n + TS_ROWS - 1) / TS_ROWS);
     note_launch(); ts_mul_kernel<<<grid, TS_THREADS, sm, s>>>(A, ka, C, cstride, O, kb, n, items, beta, alpha);
     return cudaGetLastError();
