@@ -67,9 +67,38 @@ extern "C" int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo
     int dev = 0;
     cudaGetDevice(&dev);
     cudaStream_t caller = (cudaStream_t)stream;
-    cudaEvent_t start;
-    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
-    cudaEventRecord(start, caller);
+    // the workers' streams and events; on a failure nothing has been launched
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t start = nullptr;
+    auto release = [&]() {
+        for (cudaEvent_t ev : done) cudaEventDestroy(ev);
+        for (cudaStream_t st : streams) cudaStreamDestroy(st);
+        if (start) cudaEventDestroy(start);
+    };
+    cudaError_t e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        start = nullptr;
+        return cuda_err(e, "pseudo_grid_batch: event");
+    }
+    for (int w = 0; w < nw; ++w) {
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+            release();
+            return cuda_err(e, "pseudo_grid_batch: stream");
+        }
+        streams.push_back(st);
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            release();
+            return cuda_err(e, "pseudo_grid_batch: event");
+        }
+        done.push_back(ev);
+    }
+    if ((e = cudaEventRecord(start, caller)) != cudaSuccess) {
+        release();
+        return cuda_err(e, "pseudo_grid_batch: stream");
+    }
     // largest matrices first
     std::vector<int> order(nmat);
     std::iota(order.begin(), order.end(), 0);
@@ -79,12 +108,6 @@ extern "C" int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo
     std::atomic<int> next{0};
     std::vector<int> results(nmat, PSEUDO_OK);
     std::vector<std::string> errors(nmat);
-    std::vector<cudaStream_t> streams(nw);
-    std::vector<cudaEvent_t> done(nw);
-    for (int w = 0; w < nw; ++w) {
-        cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&done[w], cudaEventDisableTiming);
-    }
     auto worker = [&](int w) {
         cudaSetDevice(dev);
         cudaStreamWaitEvent(streams[w], start, 0);
@@ -106,11 +129,7 @@ extern "C" int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo
     for (int w = 0; w < nw; ++w) pool.emplace_back(worker, w);
     for (auto &t : pool) t.join();
     for (int w = 0; w < nw; ++w) cudaStreamWaitEvent(caller, done[w], 0);
-    for (int w = 0; w < nw; ++w) {
-        cudaEventDestroy(done[w]);
-        cudaStreamDestroy(streams[w]);
-    }
-    cudaEventDestroy(start);
+    release();
     rc = PSEUDO_OK;
     for (int m = 0; m < nmat; ++m) {
         if (results[m] < 0) return set_err(results[m], "matrix %d: %s", m, errors[m].c_str());
