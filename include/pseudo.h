@@ -156,7 +156,7 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
  * points under options o.  Errors: ARG. */
 int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, size_t *bytes);
 
-/* sigma_min(T - z_j I) for j < npts.
+/* sigma_min(T - z_j I) for j < npts (0 <= npts <= 2^31 - 1).
  *   z          : npts complex shifts (device, or host if o->io_host).
  *   eps_levels : host array of neps (<= 32) levels; may be NULL if neps == 0.
  *   sigma_out  : npts doubles (device/host as z).
@@ -215,7 +215,7 @@ int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t n
  *   grid_nx, grid_ny : the layout of pseudo_opts (z[iy * grid_nx + ix]);
  *                      grid_nx = 0 means unordered points, visited in index
  *                      order.
- *   batch_b          : b; values below 1 are taken as 1, as pseudo_grid does.
+ *   batch_b          : b >= 1 (pseudo_opts.batch_b).
  *   order            : caller-owned host array of npts int32, written with the
  *                      point indices in visiting order.
  * Host-only: needs no handle and no device.  Errors: ARG. */

@@ -23,9 +23,10 @@ from __future__ import annotations
 
 
 def batch_zigzag(nx: int, ny: int, b: int) -> list[int]:
+    if b < 1:
+        raise ValueError("batch size b must be >= 1")
     if nx <= 0 or ny <= 0:
         return []
-    b = max(1, b)
     batches = []  # (batch row, sweep position, x, first y)
     for y0 in range(0, ny, b):
         row = y0 // b

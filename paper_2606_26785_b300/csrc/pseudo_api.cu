@@ -369,7 +369,7 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
     int rc = check_opts(o);
     if (rc) return rc;
-    if (npts < 0 || npts > (int64_t)1 << 31) return set_err(PSEUDO_ERR_ARG, "npts out of range");
+    if (npts < 0 || npts >= (int64_t)1 << 31) return set_err(PSEUDO_ERR_ARG, "npts out of range");
     if (npts == 0) return PSEUDO_OK;
     if (!z || !sigma_out) return set_err(PSEUDO_ERR_ARG, "z and sigma_out are required");
     if (neps < 0 || neps > 32 || (neps > 0 && !eps_levels)) return set_err(PSEUDO_ERR_ARG, "bad eps levels");

@@ -740,10 +740,10 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
 
 extern "C" int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int32_t *order) {
     using namespace pseudo;
-    if (npts < 0 || npts > INT32_MAX || grid_nx < 0 || grid_ny < 0 || (npts > 0 && !order))
+    if (npts < 0 || npts > INT32_MAX || grid_nx < 0 || grid_ny < 0 || batch_b < 1 || (npts > 0 && !order))
         return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (grid_nx > 0 && (int64_t)grid_nx * grid_ny != npts) return set_err(PSEUDO_ERR_ARG, "grid_nx * grid_ny != npts");
-    const std::vector<int> ord = batch_zigzag(npts, grid_nx, grid_ny, std::max(1, batch_b));
+    const std::vector<int> ord = batch_zigzag(npts, grid_nx, grid_ny, batch_b);
     std::copy(ord.begin(), ord.end(), order);
     return PSEUDO_OK;
 }

@@ -58,11 +58,12 @@ def test_permutation_and_step_geometry(nx, ny, b):
 def test_degenerate_grids():
     assert batch_zigzag(0, 5, 2) == []
     assert batch_zigzag(3, 0, 2) == []
-    assert batch_zigzag(3, 2, 0) == batch_zigzag(3, 2, 1)
+    with pytest.raises(ValueError):
+        batch_zigzag(3, 2, 0)
 
 
 @pytest.mark.parametrize("nx,ny,b", [(3, 4, 2), (2, 5, 2), (9, 9, 3), (200, 200, 20), (37, 53, 7), (8, 3, 1),
-                                     (5, 4, 100), (1, 1, 1), (64, 64, 0)])
+                                     (5, 4, 100), (1, 1, 1), (64, 64, 64)])
 def test_library_order_matches_oracle(nx, ny, b):
     import paper_2606_26785_b300 as p
 
@@ -80,3 +81,5 @@ def test_library_order_unordered_points_and_errors():
         p.traversal_order(3, 4, 2, npts=11)
     with pytest.raises(p.PseudoError):
         p.traversal_order(-1, 4, 2, npts=4)
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(3, 4, 0)
