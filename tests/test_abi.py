@@ -54,3 +54,61 @@ def test_errors_without_handle():
     assert lib.pseudo_info(None, None, None, None) == _abi.ERR_ARG
     assert b"NULL" in lib.pseudo_last_error()
     lib.pseudo_destroy(None)  # NULL-safe
+
+
+def test_argument_errors_are_reported_before_any_device_work():
+    """Every entry point validates its host-side arguments first: these calls
+    return their documented error codes on a machine without a GPU."""
+    from paper_2606_26785_b300 import _abi
+
+    lib = _abi.load()
+    vp, c64 = ctypes.c_void_p, ctypes.c_int64
+    buf = (ctypes.c_double * 8)()
+    h = vp()
+    # pseudo_create: NULL out, NULL T, rectangular, n out of range, ldT < n
+    assert lib.pseudo_create(buf, c64(2), c64(2), c64(2), 1, None, None) == _abi.ERR_ARG
+    assert lib.pseudo_create(None, c64(2), c64(2), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
+    assert lib.pseudo_create(buf, c64(4), c64(4), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_UNSUPPORTED
+    assert b"rectangular" in lib.pseudo_last_error()
+    assert lib.pseudo_create(buf, c64(0), c64(0), c64(0), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
+    assert lib.pseudo_create(buf, c64(1), c64(2), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
+    assert h.value is None
+    o = _abi.Opts()
+    assert lib.pseudo_opts_default(None) == _abi.ERR_ARG
+    assert lib.pseudo_opts_default(ctypes.byref(o)) == 0
+    size = ctypes.c_size_t()
+    assert lib.pseudo_workspace_bytes(None, ctypes.byref(o), c64(4), ctypes.byref(size)) == _abi.ERR_ARG
+    assert lib.pseudo_grid(None, buf, c64(4), None, 0, ctypes.byref(o), buf, None, None, None, buf,
+                           ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    n1 = (ctypes.c_int64 * 1)(4)
+    assert lib.pseudo_grid_batch_workspace_bytes(None, 1, n1, ctypes.byref(o), ctypes.byref(size)) == _abi.ERR_ARG
+    assert lib.pseudo_grid_batch(None, 0, None, n1, None, 0, ctypes.byref(o), None, None, None, None, None,
+                                 ctypes.c_size_t(0), None) == _abi.ERR_ARG
+    assert lib.pseudo_solve(None, buf, buf, c64(1), 0, 0, buf, ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    assert lib.pseudo_matvec(None, buf, None, buf, buf, c64(1), 0, 0, 0, buf, ctypes.c_size_t(64),
+                             None) == _abi.ERR_ARG
+    assert lib.pseudo_stats(None, None) == _abi.ERR_ARG
+
+
+def test_last_error_is_per_thread():
+    import threading
+
+    from paper_2606_26785_b300 import _abi
+
+    lib = _abi.load()
+    assert lib.pseudo_info(None, None, None, None) == _abi.ERR_ARG
+    mine = lib.pseudo_last_error()
+    seen = {}
+
+    def other():
+        buf = (ctypes.c_double * 8)()
+        h = ctypes.c_void_p()
+        seen["rc"] = lib.pseudo_create(buf, ctypes.c_int64(4), ctypes.c_int64(4), ctypes.c_int64(2), 1, None,
+                                       ctypes.byref(h))
+        seen["msg"] = lib.pseudo_last_error()
+
+    t = threading.Thread(target=other)
+    t.start()
+    t.join()
+    assert seen["rc"] == _abi.ERR_UNSUPPORTED and b"rectangular" in seen["msg"]
+    assert lib.pseudo_last_error() == mine and b"NULL" in mine
