@@ -83,3 +83,17 @@ def test_library_order_unordered_points_and_errors():
         p.traversal_order(-1, 4, 2, npts=4)
     with pytest.raises(p.PseudoError):
         p.traversal_order(3, 4, 0)
+
+
+def test_library_order_matches_oracle_on_random_grids():
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+
+    import paper_2606_26785_b300 as p
+
+    @settings(max_examples=300, deadline=None)
+    @given(st.integers(1, 90), st.integers(1, 90), st.integers(1, 100))
+    def check(nx, ny, b):
+        assert p.traversal_order(nx, ny, b).tolist() == batch_zigzag(nx, ny, b)
+
+    check()
