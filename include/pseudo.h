@@ -61,6 +61,13 @@ enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
 /* pseudo_solve / pseudo_matvec only: the CUDA-core kernels instead of the tensor-core ones */
 enum { PSEUDO_MIXED_CUDACORE = 2 };
 
+/* grid traversal of the recycling path (pseudo_opts.traversal):
+ * BATCH_ZIGZAG = the batch-zigzag order of Sec. 2.3 with column batches of
+ * batch_b points (default); HILBERT, MORTON = the Hilbert curve and the
+ * Z-order that Sec. 5 names as locality-preserving alternatives, on the
+ * smallest 2^q x 2^q square holding the grid, points outside it skipped. */
+enum { PSEUDO_TRAVERSE_BATCH_ZIGZAG = 0, PSEUDO_TRAVERSE_HILBERT = 1, PSEUDO_TRAVERSE_MORTON = 2 };
+
 /* per-point flags (flags_out) */
 enum {
     PSEUDO_PT_ACCEPTED = 1,      /* recycled Ritz value accepted (no refinement) */
@@ -99,6 +106,7 @@ typedef struct {
     int fp32_solver;    /* mixed precision: the FP32 triangular solves run on 0 = the tensor
                            cores (tcgen05, operands split hi + lo into TF32, 3 products),
                            1 = the CUDA cores (FP32 FMA) */
+    int traversal;      /* RECYCLE on a Cartesian grid: the visiting order, PSEUDO_TRAVERSE_* */
 } pseudo_opts;
 
 typedef struct {
@@ -203,23 +211,28 @@ int pseudo_grid_batch(const pseudo_handle *hs, int nmat, const pseudo_c64 *const
 int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t npts, int64_t *out);
 
 /* The order in which the recycling path (PSEUDO_RECYCLE) visits the points of
- * a Cartesian grid: the batch-zigzag traversal of Sec. 2.3, eq. (batch).  The
- * grid is cut into column batches of b vertically adjacent points (the top
- * batch row is shorter when b does not divide grid_ny); batch rows are taken
- * from the bottom, swept in a row-wise zigzag (the first left to right, the
- * next right to left, and so on), and the points of each batch are visited
- * bottom to top.  The recycling path splits this sequence into `lanes`
- * contiguous segments.
+ * a Cartesian grid.  PSEUDO_TRAVERSE_BATCH_ZIGZAG: the batch-zigzag traversal
+ * of Sec. 2.3, eq. (batch): the grid is cut into column batches of b
+ * vertically adjacent points (the top batch row is shorter when b does not
+ * divide grid_ny); batch rows are taken from the bottom, swept in a row-wise
+ * zigzag (the first left to right, the next right to left, and so on), and
+ * the points of each batch are visited bottom to top.  PSEUDO_TRAVERSE_HILBERT
+ * and PSEUDO_TRAVERSE_MORTON (Sec. 5): the Hilbert curve from (0, 0) to
+ * (2^q - 1, 0), resp. the Z-order (x in the low bit), on the smallest 2^q x
+ * 2^q square holding the grid, with the points outside the grid skipped.
+ * The recycling path splits this sequence into `lanes` contiguous segments.
  *   npts             : number of points; must equal grid_nx * grid_ny when
  *                      grid_nx > 0 (at most 2^31 - 1).
  *   grid_nx, grid_ny : the layout of pseudo_opts (z[iy * grid_nx + ix]);
  *                      grid_nx = 0 means unordered points, visited in index
  *                      order.
- *   batch_b          : b >= 1 (pseudo_opts.batch_b).
+ *   batch_b          : b >= 1 (pseudo_opts.batch_b; used by the batch zigzag).
+ *   traversal        : PSEUDO_TRAVERSE_* (pseudo_opts.traversal).
  *   order            : caller-owned host array of npts int32, written with the
  *                      point indices in visiting order.
  * Host-only: needs no handle and no device.  Errors: ARG. */
-int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int32_t *order);
+int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int traversal,
+                           int32_t *order);
 
 /* Counters and phase timings accumulated since create or the last reset. */
 int pseudo_stats(pseudo_handle h, pseudo_stats_t *out);

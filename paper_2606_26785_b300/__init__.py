@@ -11,9 +11,12 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, Opts, PseudoError, Stats, check  # noqa: F401
+from ._abi import (  # noqa: F401
+    FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON, Opts,
+    PseudoError, Stats, check)
 
-__all__ = ["Pseudo", "grid_batch", "traversal_order", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE", "INVLANC", "RECYCLE", "PseudoError"]
+__all__ = ["Pseudo", "grid_batch", "traversal_order", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE", "INVLANC",
+           "RECYCLE", "TRAVERSE_BATCH_ZIGZAG", "TRAVERSE_HILBERT", "TRAVERSE_MORTON", "PseudoError"]
 
 
 def default_opts(**kw) -> Opts:
@@ -245,12 +248,14 @@ def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=N
     return outs, rc
 
 
-def traversal_order(grid_nx: int, grid_ny: int, batch_b: int, npts: int | None = None) -> np.ndarray:
+def traversal_order(grid_nx: int, grid_ny: int, batch_b: int = 20, traversal: int = TRAVERSE_BATCH_ZIGZAG,
+                    npts: int | None = None) -> np.ndarray:
     """Point indices in the order the recycling path visits a grid_nx x
     grid_ny grid (z[iy * grid_nx + ix]): the batch-zigzag traversal of Sec.
-    2.3 with column batches of batch_b points (pseudo_traversal_order)."""
+    2.3 with column batches of batch_b points, or the Hilbert / Morton order
+    of Sec. 5 (pseudo_traversal_order)."""
     n = grid_nx * grid_ny if npts is None else int(npts)
     out = np.empty(n, dtype=np.int32)
-    check(_abi.load().pseudo_traversal_order(ctypes.c_int64(n), grid_nx, grid_ny, batch_b,
+    check(_abi.load().pseudo_traversal_order(ctypes.c_int64(n), grid_nx, grid_ny, batch_b, traversal,
                                              out.ctypes.data_as(ctypes.c_void_p)))
     return out

@@ -11,6 +11,7 @@ WARN_NOT_CONVERGED = 1
 ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 INVLANC, RECYCLE = 0, 1
 FP64, MIXED, MIXED_CUDACORE = 0, 1, 2
+TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON = 0, 1, 2
 PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4, 8, 16
 
 EXPORTED = (
@@ -30,6 +31,7 @@ class Opts(ctypes.Structure):
         ("omega", ctypes.c_double), ("eta", ctypes.c_double), ("rtol", ctypes.c_double),
         ("maxiter_lanczos", ctypes.c_int), ("maxiter_lobpcg", ctypes.c_int), ("max_ir", ctypes.c_int),
         ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("fp32_solver", ctypes.c_int),
+        ("traversal", ctypes.c_int),
     ]
 
 

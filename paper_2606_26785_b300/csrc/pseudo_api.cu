@@ -336,6 +336,8 @@ static int check_opts(const pseudo_opts *o) {
         if (!(o->omega >= 1.0)) return set_err(PSEUDO_ERR_ARG, "omega must be >= 1");
         if (o->batch_b < 1) return set_err(PSEUDO_ERR_ARG, "batch_b must be >= 1");
         if (o->grid_nx < 0 || o->grid_ny < 0) return set_err(PSEUDO_ERR_ARG, "bad grid dims");
+        if (o->traversal < PSEUDO_TRAVERSE_BATCH_ZIGZAG || o->traversal > PSEUDO_TRAVERSE_MORTON)
+            return set_err(PSEUDO_ERR_ARG, "bad traversal %d", o->traversal);
     }
     return PSEUDO_OK;
 }

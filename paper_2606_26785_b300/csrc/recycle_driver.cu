@@ -303,6 +303,69 @@ static std::vector<int> batch_zigzag(int64_t npts, int nx, int ny, int b) {
     return ord;
 }
 
+// Side of the smallest 2^q x 2^q square holding an nx x ny grid.
+static int64_t curve_side(int nx, int ny) {
+    int64_t side = 1;
+    while (side < std::max(nx, ny)) side <<= 1;
+    return side;
+}
+
+// Hilbert order (Sec. 5): the curve of side 2^q that runs from (0, 0) to
+// (side - 1, 0), points outside the grid skipped.  Position d on the curve is
+// mapped to (x, y) two bits at a time, from the smallest sub-square up: the
+// two bits pick the quadrant, and the part already built is transposed (lower
+// left) or reflected in the anti-diagonal (lower right) before being moved
+// into it.
+static std::vector<int> hilbert_order(int nx, int ny) {
+    const int64_t side = curve_side(nx, ny);
+    std::vector<int> ord;
+    ord.reserve((size_t)nx * ny);
+    for (int64_t d = 0; d < side * side; ++d) {
+        int64_t x = 0, y = 0, t = d;
+        for (int64_t s = 1; s < side; s <<= 1, t >>= 2) {
+            const int64_t qx = (t >> 1) & 1, qy = (t ^ qx) & 1;
+            if (qy == 0) {
+                if (qx == 1) {
+                    x = s - 1 - x;
+                    y = s - 1 - y;
+                }
+                std::swap(x, y);
+            }
+            x += s * qx;
+            y += s * qy;
+        }
+        if (x < nx && y < ny) ord.push_back((int)(y * nx + x));
+    }
+    return ord;
+}
+
+// Morton (Z-order, Sec. 5): points sorted by the interleaving of the bits of
+// ix (even bit positions) and iy (odd positions).
+static std::vector<int> morton_order(int nx, int ny) {
+    auto spread = [](uint64_t v) {
+        uint64_t r = 0;
+        for (int b = 0; b < 32; ++b) r |= ((v >> b) & 1ull) << (2 * b);
+        return r;
+    };
+    std::vector<std::pair<uint64_t, int>> key;
+    key.reserve((size_t)nx * ny);
+    for (int iy = 0; iy < ny; ++iy)
+        for (int ix = 0; ix < nx; ++ix) key.emplace_back(spread(ix) | (spread(iy) << 1), iy * nx + ix);
+    std::sort(key.begin(), key.end());
+    std::vector<int> ord(key.size());
+    for (size_t i = 0; i < key.size(); ++i) ord[i] = key[i].second;
+    return ord;
+}
+
+// The recycling path's visiting order for the chosen traversal.
+static std::vector<int> grid_order(int64_t npts, int nx, int ny, int b, int traversal) {
+    if (nx > 0 && ny > 0) {
+        if (traversal == PSEUDO_TRAVERSE_HILBERT) return hilbert_order(nx, ny);
+        if (traversal == PSEUDO_TRAVERSE_MORTON) return morton_order(nx, ny);
+    }
+    return batch_zigzag(npts, nx, ny, b);
+}
+
 // FP64-corrected inverse-iteration polish of cnt unit vectors U (n x cnt)
 // with shifts zc, followed by the Rayleigh quotient s2 and residual rr.
 static cudaError_t polish_and_rq(pseudo_ctx *h, RecyLayout &R, int cnt, int polish, int max_ir,
@@ -609,7 +672,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     cudaMemsetAsync(R.p, 0, sizeof(int) * R.L, s);
     // traversal and lane segments
     const int tb = std::max(1, o->batch_b);  // column-batch size of the traversal
-    const std::vector<int> ord = batch_zigzag(npts, o->grid_nx, o->grid_ny, tb);
+    const std::vector<int> ord = grid_order(npts, o->grid_nx, o->grid_ny, tb, o->traversal);
     std::vector<int64_t> seg(R.L + 1);
     {
         const int64_t nbat = (npts + tb - 1) / tb;
@@ -738,12 +801,15 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
 
 }  // namespace pseudo
 
-extern "C" int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int32_t *order) {
+extern "C" int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int traversal,
+                                      int32_t *order) {
     using namespace pseudo;
     if (npts < 0 || npts > INT32_MAX || grid_nx < 0 || grid_ny < 0 || batch_b < 1 || (npts > 0 && !order))
         return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (traversal < PSEUDO_TRAVERSE_BATCH_ZIGZAG || traversal > PSEUDO_TRAVERSE_MORTON)
+        return set_err(PSEUDO_ERR_ARG, "bad traversal %d", traversal);
     if (grid_nx > 0 && (int64_t)grid_nx * grid_ny != npts) return set_err(PSEUDO_ERR_ARG, "grid_nx * grid_ny != npts");
-    const std::vector<int> ord = batch_zigzag(npts, grid_nx, grid_ny, batch_b);
+    const std::vector<int> ord = grid_order(npts, grid_nx, grid_ny, batch_b, traversal);
     std::copy(ord.begin(), ord.end(), order);
     return PSEUDO_OK;
 }

@@ -62,6 +62,45 @@ def test_degenerate_grids():
         batch_zigzag(3, 2, 0)
 
 
+@pytest.mark.parametrize("nx,ny,b", [(3, 4, 2), (2, 5, 2), (9, 9, 3), (200, 200, 20), (37, 53, 7), (8, 3, 1),
+                                     (5, 4, 100), (1, 1, 1), (64, 64, 64)])
+def test_library_order_matches_oracle(nx, ny, b):
+    import paper_2606_26785_b300 as p
+
+    got = p.traversal_order(nx, ny, b)
+    assert got.dtype == np.int32
+    assert got.tolist() == batch_zigzag(nx, ny, b)
+
+
+def test_library_order_unordered_points_and_errors():
+    import paper_2606_26785_b300 as p
+
+    assert p.traversal_order(0, 0, 4, npts=6).tolist() == list(range(6))
+    assert p.traversal_order(0, 0, 4, npts=0).tolist() == []
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(3, 4, 2, npts=11)
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(-1, 4, 2, npts=4)
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(3, 4, 0)
+
+
+def test_library_order_matches_oracle_on_random_grids():
+    from hypothesis import given, settings
+    from hypothesis import strategies as st
+
+    import paper_2606_26785_b300 as p
+
+    @settings(max_examples=300, deadline=None)
+    @given(st.integers(1, 90), st.integers(1, 90), st.integers(1, 100))
+    def check(nx, ny, b):
+        assert p.traversal_order(nx, ny, b).tolist() == batch_zigzag(nx, ny, b)
+        assert p.traversal_order(nx, ny, b, p.TRAVERSE_HILBERT).tolist() == hilbert(nx, ny)
+        assert p.traversal_order(nx, ny, b, p.TRAVERSE_MORTON).tolist() == morton(nx, ny)
+
+    check()
+
+
 # ------------------------------------------------ Hilbert and Morton (Sec. 5)
 
 
@@ -109,3 +148,19 @@ def test_curves_on_rectangles_are_the_square_curve_cropped(nx, ny):
     for f in (hilbert, morton):
         full = _xy(f(side, side), side)
         assert _xy(f(nx, ny), nx) == [(x, y) for x, y in full if x < nx and y < ny]
+
+
+@pytest.mark.parametrize("nx,ny", [(3, 4), (9, 9), (40, 40), (37, 53), (1, 1), (200, 200), (64, 3)])
+def test_library_hilbert_and_morton_match_oracle(nx, ny):
+    import paper_2606_26785_b300 as p
+
+    assert p.traversal_order(nx, ny, 20, p.TRAVERSE_HILBERT).tolist() == hilbert(nx, ny)
+    assert p.traversal_order(nx, ny, 20, p.TRAVERSE_MORTON).tolist() == morton(nx, ny)
+
+
+def test_library_traversal_errors_and_unordered_points():
+    import paper_2606_26785_b300 as p
+
+    with pytest.raises(p.PseudoError):
+        p.traversal_order(4, 4, 2, 3)
+    assert p.traversal_order(0, 0, 2, p.TRAVERSE_HILBERT, npts=5).tolist() == list(range(5))
