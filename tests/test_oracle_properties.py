@@ -1,0 +1,53 @@
+"""Randomised pins of the CPU oracle (hypothesis): on arbitrary small complex
+matrices and shifts, the oracle's singular values agree with an independent
+library SVD, and sigma_min obeys the bounds the mathematics fixes (distance
+to the spectrum, Weyl's perturbation bound, the Frobenius identity)."""
+import numpy as np
+import pytest
+from hypothesis import given, settings
+from hypothesis import strategies as st
+
+import oracle
+
+pytestmark = pytest.mark.filterwarnings("ignore")
+
+finite = st.floats(-4.0, 4.0, allow_nan=False, allow_infinity=False)
+
+
+@st.composite
+def matrix_and_shift(draw):
+    n = draw(st.integers(1, 7))
+    re = np.array(draw(st.lists(finite, min_size=n * n, max_size=n * n))).reshape(n, n)
+    im = np.array(draw(st.lists(finite, min_size=n * n, max_size=n * n))).reshape(n, n)
+    z = complex(draw(finite), draw(finite))
+    return re + 1j * im, z
+
+
+@settings(max_examples=150, deadline=None)
+@given(matrix_and_shift())
+def test_matches_library_svd_and_frobenius(case):
+    C, z = case
+    n = C.shape[0]
+    B = C - z * np.eye(n)
+    s, _ = oracle.singular_values(C, z)
+    ref = np.sort(np.linalg.svd(B, compute_uv=False))
+    scale = max(np.linalg.norm(B, 2), 1e-300)
+    assert np.all(np.diff(s) >= 0)
+    assert np.max(np.abs(s - ref)) <= 64 * n * 2.2e-16 * scale + 1e-300
+    assert abs(np.sum(s ** 2) - np.linalg.norm(B) ** 2) <= 64 * n * 2.2e-16 * np.linalg.norm(B) ** 2 + 1e-300
+
+
+@settings(max_examples=100, deadline=None)
+@given(matrix_and_shift(), finite, finite)
+def test_distance_and_weyl_bounds(case, dx, dy):
+    C, z = case
+    n = C.shape[0]
+    lam = np.linalg.eigvals(C)
+    smin = oracle.singular_values(C, z)[0][0]
+    tol = 64 * n * 2.2e-16 * max(np.linalg.norm(C - z * np.eye(n), 2), 1.0)
+    # sigma_min(C - zI) <= |lambda - z| for every eigenvalue lambda
+    assert smin <= np.min(np.abs(lam - z)) + tol + 1e-9 * np.linalg.norm(C, 2)
+    # Weyl: |sigma_min(C - zI) - sigma_min(C - wI)| <= |z - w|
+    w = z + 0.1 * complex(dx, dy)
+    smin_w = oracle.singular_values(C, w)[0][0]
+    assert abs(smin - smin_w) <= abs(z - w) + 2 * tol
