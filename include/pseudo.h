@@ -289,11 +289,14 @@ int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pse
  * Scratch: a fixed 16 MiB array inside the library (2^20 complex doubles), held
  * by every GPU that loads the library until the process exits.  The solve needs
  * ceil(ncols / 8) * n_pad * 8 of its elements (n_pad = n rounded up to 128), so
- * n = 2000 allows up to 512 columns per call; larger calls return
- * PSEUDO_ERR_ARG with a message and launch nothing.
+ * n = 2000 allows up to 512 columns per call; larger calls (and any ncols
+ * above 2^20) return PSEUDO_ERR_ARG with a message and launch nothing.
  * The first call on a device looks up the array's device address (with the
  * handle's device current, which the call requires); make that first call
- * before any stream capture.  All calls share the one array: calls whose work
+ * before any stream capture.  The address is kept for the life of the
+ * process: after a device reset (cudaDeviceReset, or anything else that tears
+ * down the primary context) it is stale, so do not call this entry point
+ * again in that process.  All calls share the one array: calls whose work
  * overlaps on the GPU (other streams, other threads) race and corrupt each
  * other's results, so serialise them.  The array keeps the last call's
  * contents; the solve writes every scratch row before reading it, so nothing

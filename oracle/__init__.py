@@ -70,6 +70,9 @@ def _load():
                                               dp, ctypes.c_int64, dp, dp, ctypes.c_int]
         lib.oracle_sigma_min_grid.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_jacobi_rounds.argtypes = [dp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_jacobi_rounds.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -85,9 +88,10 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
-def singular_values(C, z: complex, threads: int = 1):
+def singular_values(C, z: complex, threads: int = 1, return_sweeps: bool = False):
     """All singular values of C - z I (ascending) and the oracle's final
-    relative off-orthogonality.  C is m x n with m >= n; for m > n, I is the
+    relative off-orthogonality (and, with ``return_sweeps``, the number of
+    Jacobi sweeps it took).  C is m x n with m >= n; for m > n, I is the
     m x n rectangular identity (Sec. 1)."""
     lib = _load()
     A = _as_fortran_c128(C)
@@ -101,7 +105,22 @@ def singular_values(C, z: complex, threads: int = 1):
                                sig.ctypes.data_as(dp), off.ctypes.data_as(dp), int(threads))
     if s < 0:
         raise RuntimeError("oracle Jacobi SVD did not converge")
+    if return_sweeps:
+        return sig, float(off[0]), int(s)
     return sig, float(off[0])
+
+
+def jacobi_rounds(C, z: complex, rounds: int, threads: int = 1):
+    """Run only the first ``rounds`` rounds of the oracle's Jacobi iteration
+    on C - z I (each round: n/2 disjoint column-pair rotations) and return
+    nothing.  A timing sample for matrices where a whole point takes hours: a
+    full point takes sweeps * (n - 1 + n % 2) rounds."""
+    lib = _load()
+    A = _as_fortran_c128(C)
+    m, n = A.shape
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_jacobi_rounds(A.ctypes.data_as(dp), m, m, n, float(np.real(z)), float(np.imag(z)), int(rounds),
+                             int(threads))
 
 
 def sigma_min_grid(C, z, threads: int | None = None):

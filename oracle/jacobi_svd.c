@@ -86,18 +86,23 @@ static int cmp_double(const void *a, const void *b) {
 /* Jacobi SVD of the m x n matrix held in A (overwritten).  Writes the n
  * singular values in ascending order and returns the number of sweeps; *off
  * receives the largest relative off-orthogonality seen in the final sweep.
- * nthreads > 1 parallelises the disjoint pairs of each round. */
+ * nthreads > 1 parallelises the disjoint pairs of each round.  max_rounds >= 0
+ * stops after that many rounds (a timing sample; the values are then not the
+ * converged ones); -1 = no limit. */
 static int jacobi_sweeps(ormat *A, double tol, int max_sweeps, int nthreads, double *sigma,
-                         double *off) {
+                         double *off, int64_t max_rounds) {
     int64_t n = A->n;
     int64_t np = (n % 2) ? n + 1 : n; /* odd n: one dummy column sits out */
     int64_t *ring = (int64_t *)malloc(sizeof(int64_t) * np);
     for (int64_t k = 0; k < np; k++) ring[k] = k;
     int sweep = 0;
     double worst = 0.0;
+    int64_t rounds_done = 0;
     for (sweep = 0; sweep < max_sweeps; sweep++) {
         worst = 0.0;
         for (int64_t round = 0; round < np - 1; round++) {
+            if (max_rounds >= 0 && rounds_done >= max_rounds) break;
+            rounds_done++;
             double wr = 0.0;
             int64_t half = np / 2;
 #ifdef _OPENMP
@@ -116,6 +121,7 @@ static int jacobi_sweeps(ormat *A, double tol, int max_sweeps, int nthreads, dou
             for (int64_t k = np - 1; k > 1; k--) ring[k] = ring[k - 1];
             ring[1] = last;
         }
+        if (max_rounds >= 0 && rounds_done >= max_rounds) break;
         if (worst <= tol) { sweep++; break; }
     }
     free(ring);
@@ -149,9 +155,33 @@ int oracle_svd_shifted(const double *C, int64_t ldc, int64_t m, int64_t n, doubl
     for (int64_t j = 0; j < n && j < m; j++) { A.re[j * m + j] -= zr; A.im[j * m + j] -= zi; }
     double tol = (double)m * 2.220446049250313e-16;
     int max_sweeps = 60;
-    int sweeps = jacobi_sweeps(&A, tol, max_sweeps, nthreads, sigma, off);
+    int sweeps = jacobi_sweeps(&A, tol, max_sweeps, nthreads, sigma, off, -1);
     free(A.re); free(A.im);
     return (*off <= tol) ? sweeps : -1;
+}
+
+/* Timing sample of the oracle for matrices where one point takes hours: the
+ * first `rounds` rounds (each n/2 disjoint pair rotations, about 1/(n-1) of a
+ * sweep) of the Jacobi iteration above on C - zI, with nothing else changed.
+ * A full point takes sweeps * (n - 1 + n % 2) rounds, with sweeps as
+ * returned by oracle_svd_shifted.  Returns 0. */
+int oracle_jacobi_rounds(const double *C, int64_t ldc, int64_t m, int64_t n, double zr, double zi,
+                         int64_t rounds, int nthreads) {
+    ormat A;
+    A.m = m; A.n = n;
+    A.re = (double *)malloc(sizeof(double) * m * n);
+    A.im = (double *)malloc(sizeof(double) * m * n);
+    double *sigma = (double *)malloc(sizeof(double) * n);
+    double off;
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = 0; i < m; i++) {
+            A.re[j * m + i] = C[2 * (j * ldc + i)];
+            A.im[j * m + i] = C[2 * (j * ldc + i) + 1];
+        }
+    for (int64_t j = 0; j < n && j < m; j++) { A.re[j * m + j] -= zr; A.im[j * m + j] -= zi; }
+    jacobi_sweeps(&A, (double)m * 2.220446049250313e-16, 60, nthreads, sigma, &off, rounds);
+    free(A.re); free(A.im); free(sigma);
+    return 0;
 }
 
 /* sigma_min(C - z_p I) for npts shifts.  Points are spread over OpenMP

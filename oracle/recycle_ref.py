@@ -15,8 +15,12 @@ infrastructure only).
 
 Library primitives (numpy eigh / qr / svd) serve as the steps the paper
 names ``eig``, ``qr``, ``svd``.  Pinned in tests/test_oracle_recycle.py by the
-full-basis exactness of the Ritz value, the Courant--Fischer upper bound and
-the QL / auxiliary-matrix invariants after updates.
+full-basis exactness of the Ritz value, the Courant--Fischer upper bound, the
+QL / auxiliary-matrix invariants after updates, hand-built eigenvalue sets
+with a known r~ (``rtilde``: gaps on both sides of the threshold, at j = r,
+at j = pr - 1, equal to it, none qualifying) and hand-built bases with known
+projection errors rho_j and a known pruning count (``prune_count``: first
+violation, never violated, a ratio equal to omega, the p_max cap).
 """
 from __future__ import annotations
 
@@ -70,6 +74,21 @@ class RecycleState:
         return {k: v / (scale if k in ("W3", "H1") else max(1.0, np.linalg.norm(T))) for k, v in errs.items()}, n
 
 
+def rtilde(theta, r: int, tau: float) -> int:
+    """Alg. 1 step 2, eq. (tau): the smallest j with r <= j < pr (1-based)
+    whose eigen-gap |theta_j - theta_{j+1}| exceeds theta_pr * eps_m / tau,
+    for the ascending eigenvalues theta of H(z) (pr = len(theta)).  When no
+    gap qualifies (the paper's minimum over an empty set) the whole basis is
+    kept: r~ = pr."""
+    theta = np.asarray(theta, dtype=np.float64)
+    k = theta.size
+    thresh = theta[-1] * EPS_M / tau
+    for j in range(r, k):  # 1-based j in [r, pr-1] <-> theta[j-1], theta[j]
+        if abs(theta[j - 1] - theta[j]) > thresh:
+            return j
+    return k
+
+
 def recy_sing(st: RecycleState, z: complex, eps: float, tau: float):
     """Alg. 1.  Returns dict with xi (ascending, first r), X (n x r), the
     residual norms ||W~_{:,j}||, r~ and theta."""
@@ -79,11 +98,7 @@ def recy_sing(st: RecycleState, z: complex, eps: float, tau: float):
     H = st.H1 - z * st.H2 - zc * st.H2.conj().T + (abs(z) ** 2 + eps) * np.eye(k)
     H = 0.5 * (H + H.conj().T)
     theta, G = np.linalg.eigh(H)  # ascending
-    rt = k
-    for j in range(r, k):  # 1-based j in [r, pr-1] <-> theta[j-1], theta[j]
-        if abs(theta[j - 1] - theta[j]) > theta[-1] * EPS_M / tau:
-            rt = j
-            break
+    rt = rtilde(theta, r, tau)
     Gr = G[:, :rt]
     Y = (W1 - z * V) @ Gr
     _, Rt = np.linalg.qr(Y)
@@ -97,6 +112,32 @@ def recy_sing(st: RecycleState, z: complex, eps: float, tau: float):
     return {"xi": xi, "X": X, "C": C, "wnorm": np.linalg.norm(Wt, axis=0), "rt": rt, "theta": theta}
 
 
+def prune_count(V: np.ndarray, x1: np.ndarray, r: int, omega: float, p_max: int) -> int:
+    """Alg. 2 steps 2-8 with eq. (omegaCond): how many leading r-column
+    blocks of V to drop before x1 (n x r-breve, the leading columns of the new
+    block) is appended.  rho_0 is the part of x1 outside span V, rho_j the
+    part outside the span of the blocks j+1..p; the loop stops at the first j
+    with rho_j / rho_0 > omega and l = j - 1, or l = p when it never stops
+    (rho_j only grows with j, so this l is the largest j for which eq.
+    (omegaCond) holds).  The cap of p_max blocks then raises l to
+    p + 1 - p_max if needed.  Returns -1 when x1 already lies in span V
+    (rho_0 <= 1e-12 ||x1||; nothing is appended)."""
+    p = V.shape[1] // r
+    rho0 = np.linalg.norm(x1 - V @ (V.conj().T @ x1))
+    if rho0 <= 1e-12 * np.linalg.norm(x1):
+        return -1
+    l = p
+    for j in range(1, p + 1):
+        Vj = V[:, j * r:]
+        rhoj = np.linalg.norm(x1 - Vj @ (Vj.conj().T @ x1))
+        if rhoj / rho0 > omega:
+            l = j - 1
+            break
+    if p - l + 1 > p_max:
+        l = p + 1 - p_max
+    return l
+
+
 def update_recy(st: RecycleState, X: np.ndarray, omega: float, p_max: int, rb: int = 1):
     """Alg. 2 for the new block X (n x r).  Returns (l, skipped)."""
     T, r = st.T, st.r
@@ -106,20 +147,9 @@ def update_recy(st: RecycleState, X: np.ndarray, omega: float, p_max: int, rb: i
         _refresh_aux_for(st)
         return 0, False
     p = st.p
-    x1 = X[:, :rb]
-    c = st.V.conj().T @ x1
-    rho0 = np.linalg.norm(x1 - st.V @ c)
-    if rho0 <= 1e-12 * np.linalg.norm(x1):
+    l = prune_count(st.V, X[:, :rb], r, omega, p_max)
+    if l < 0:
         return -1, True
-    l = p
-    for j in range(1, p + 1):
-        Vj = st.V[:, j * r:]
-        rhoj = np.linalg.norm(x1 - Vj @ (Vj.conj().T @ x1))
-        if rhoj / rho0 > omega:
-            l = j - 1
-            break
-    if p - l + 1 > p_max:
-        l = p + 1 - p_max
     lr = l * r
     # drop the first l blocks
     V = st.V[:, lr:]

@@ -11,6 +11,7 @@ namespace pseudo {
 constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
 int set_err(int code, const char *fmt, ...);
 int cuda_err(cudaError_t e, const char *where);
+void clear_err();
 
 // Bump allocator over the caller's workspace (256-byte aligned pieces).  With
 // a null base it only measures.

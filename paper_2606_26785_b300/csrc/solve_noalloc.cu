@@ -25,7 +25,9 @@ static __device__ __align__(256) double2 g_noalloc_scratch[NOALLOC_SCRATCH_ELEMS
 
 // In host code g_noalloc_scratch names a host-side stand-in, not the device
 // array, so its device address is looked up once per device (with that
-// device current) and cached here.
+// device current) and cached here.  The cache does not survive a device
+// reset (cudaDeviceReset or a teardown of the primary context unloads the
+// module): the header tells callers not to use this entry point after one.
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static double2 *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 static std::mutex g_noalloc_mu;
@@ -49,8 +51,15 @@ using namespace pseudo;
 
 extern "C" int pseudo_solve_noalloc(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
                                     void *stream) {
+    clear_err();
     if (!h || !X || !z || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (ncols == 0) return PSEUDO_OK;
+    // Each group of 8 columns needs at least 128 scratch elements, so more
+    // than NOALLOC_SCRATCH_ELEMS columns can never fit; rejecting them here
+    // also keeps the size product below from overflowing.
+    if ((uint64_t)ncols > NOALLOC_SCRATCH_ELEMS)
+        return set_err(PSEUDO_ERR_ARG, "pseudo_solve_noalloc: %lld columns exceed the fixed scratch of %zu elements",
+                       (long long)ncols, NOALLOC_SCRATCH_ELEMS);
     int cur = -1;
     cudaError_t e = cudaGetDevice(&cur);
     if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");

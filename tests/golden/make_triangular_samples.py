@@ -1,9 +1,15 @@
 """Write oracle reference values at a few grid points of the strongly
 nonnormal triangular workload (n = 8000, seed 3; 300 x 300 grid over
 [-1.5, 1.5]^2).  Calls only ``oracle`` (one-sided Jacobi SVD of C - zI with
-C := T, dense) and the seeded generators.  Each point costs tens of minutes
-on a few cores, so only a handful of points (seeded choice, seed 13) are
-stored.
+C := T, dense) and the seeded generators.
+
+Points: the midpoints of the bottom and left grid edges and two opposite
+corners, in that order.  Inside the unit disk that holds the spectrum this
+matrix has sigma_min far below the parity floor 1e-8 ||T||_F (about 1e-31 at
+the centre), so the sample sits on the grid's rim, where sigma_min is of
+order 1e-3 (edge midpoints) and 5e-2 (corners).  Each point costs one to two
+hours on a few host cores, so the file is rewritten after every point and a
+partial file is a valid (shorter) sample.
 
     python tests/golden/make_triangular_samples.py [count] [n] [nx]
 """
@@ -21,27 +27,36 @@ import oracle  # noqa: E402
 from paper_2606_26785_b300 import workloads  # noqa: E402
 
 
+def rim_points(nx):
+    mid = nx // 2
+    # (ix, iy): bottom-edge midpoint, left-edge midpoint, top-right and bottom-left corners
+    return [(mid, 0), (0, mid), (nx - 1, nx - 1), (0, 0)]
+
+
 def main():
-    count = int(sys.argv[1]) if len(sys.argv) > 1 else 2
+    count = int(sys.argv[1]) if len(sys.argv) > 1 else 4
     n = int(sys.argv[2]) if len(sys.argv) > 2 else 8000
     nx = int(sys.argv[3]) if len(sys.argv) > 3 else 300
     T = workloads.triangular(n, 3)
     z = workloads.grid(-1.5, 1.5, -1.5, 1.5, nx, nx)
-    rng = np.random.Generator(np.random.PCG64(13))
-    idx = sorted(int(i) for i in rng.choice(z.size, size=count, replace=False))
-    res = []
+    idx = [iy * nx + ix for ix, iy in rim_points(nx)[:count]]
+    path = Path(__file__).resolve().parent / f"triangular{n}_samples.json"
+    done = []
     t0 = time.time()
     for i in idx:
-        s, off = oracle.sigma_min_grid(T, z[[i]])
-        res.append((float(s[0]), float(off[0])))
-        print(i, res[-1], time.time() - t0, flush=True)
-    out = {"workload": f"triangular n={n} seed=3 grid {nx}x{nx} over [-1.5,1.5]^2", "n": n, "nx": nx, "ny": nx,
-           "index": idx, "z": [[float(z[i].real), float(z[i].imag)] for i in idx],
-           "sigma_ref": [r[0] for r in res], "oracle_off": [r[1] for r in res],
-           "fro_norm": float(np.linalg.norm(T)), "oracle_seconds": time.time() - t0,
-           "oracle_threads": oracle.max_threads()}
-    path = Path(__file__).resolve().parent / f"triangular{n}_samples.json"
-    path.write_text(json.dumps(out, indent=1))
+        t1 = time.time()
+        sig, off, sweeps = oracle.singular_values(T, z[i], threads=oracle.max_threads(), return_sweeps=True)
+        done.append((i, float(sig[0]), float(off), time.time() - t1, sweeps))
+        out = {"workload": f"triangular n={n} seed=3 grid {nx}x{nx} over [-1.5,1.5]^2", "n": n, "nx": nx,
+               "ny": nx, "index": [d[0] for d in done],
+               "z": [[float(z[d[0]].real), float(z[d[0]].imag)] for d in done],
+               "sigma_ref": [d[1] for d in done], "oracle_off": [d[2] for d in done],
+               "fro_norm": float(np.linalg.norm(T)), "schur_err": 0.0,
+               "oracle_seconds_per_point": [d[3] for d in done], "oracle_sweeps": [d[4] for d in done],
+               "oracle_seconds": time.time() - t0,
+               "oracle_threads": oracle.max_threads()}
+        path.write_text(json.dumps(out, indent=1))
+        print(i, done[-1], flush=True)
     print(path)
 
 

@@ -11,7 +11,10 @@ import oracle
 
 pytestmark = pytest.mark.filterwarnings("ignore")
 
-finite = st.floats(-4.0, 4.0, allow_nan=False, allow_infinity=False)
+# The oracle reads singular values off squared column norms, which underflow
+# for entries below about 1e-154 in magnitude; no workload comes near that, so
+# the drawn entries are 0 or at least 1e-100 in magnitude.
+finite = st.floats(-4.0, 4.0, allow_nan=False, allow_infinity=False).map(lambda x: 0.0 if abs(x) < 1e-100 else x)
 
 
 @st.composite

@@ -13,7 +13,7 @@ N = 50
 
 def _ref(k=200, seed=0):
     rng = np.random.default_rng(seed)
-    return 10.0 ** rng.uniform(-6, 0, k)  # all above the 1e-7 floor
+    return 10.0 ** rng.uniform(-6, -5.2, k)  # above the 1e-7 floor, below 1e-6 ||C||_F = 1e-5
 
 
 def _kw(rtol=1e-8):
@@ -73,3 +73,22 @@ def test_membership_mismatch_and_in_band_flips():
     near[3] ^= np.uint32(2)  # sigma within 1e-12 of level 1e-3: inside the band, forgiven and counted
     rep = check_sigma(ref, ref, eps_levels=eps, member=near, **_kw())
     assert rep["member_mismatch"] == 0 and rep["member_inband_flips"] == 1
+
+
+def test_relative_target_holds_alone_above_1e_6_fro():
+    # sigma_ref >= 1e-6 ||C||_F = 1e-5: atol no longer widens the band
+    ref = np.array([2e-5, 1e-3, 0.5])
+    atol = atol_for(N, FRO, 0.0, np.zeros(1))
+    assert atol > 1e-8 * ref[0]  # the combined band alone would accept the planted error below
+    sig = ref * (1 + 2e-8)
+    rep = check_sigma(sig, ref, **_kw())
+    assert rep["n_rel_only"] == 3 and rep["n_bad_rel"] == 3 and rep["n_bad"] == 3
+    ok = ref * (1 + 0.9e-8)
+    rep = check_sigma(ok, ref, **_kw())
+    assert rep["n_bad"] == 0 and rep["max_rel_err_rel_only"] < 1e-8
+    # just below the 1e-6 ||C||_F line the combined band applies
+    rep = check_sigma(np.array([9.9e-6 * (1 + 2e-8)]), np.array([9.9e-6]), **_kw())
+    assert rep["n_rel_only"] == 0 and rep["n_bad"] == 0
+    # FP64 target
+    rep = check_sigma(ref * (1 + 2e-10), ref, **_kw(rtol=1e-10))
+    assert rep["n_bad_rel"] == 3

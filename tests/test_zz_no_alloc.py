@@ -1,13 +1,15 @@
 """pseudo_solve_noalloc: the FP64 multi-shift solve for callers that cannot
 allocate device memory (it runs on a fixed scratch array inside the library
 instead of a caller workspace).  Checked through the C ABI against
-pseudo_solve on two calls in a row, with different inputs, so that the second
-call runs on the scratch contents the first one left behind.  This file is
-collected last on purpose."""
+pseudo_solve and against the oracle's textbook substitution on two calls in a
+row, with different inputs, so that the second call runs on the scratch
+contents the first one left behind.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
 import pytest
+
+from oracle import steps
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +56,9 @@ def test_noalloc_solve_matches_workspace_solve_twice(adjoint):
         got, want = X.cpu().numpy(), ref.cpu().numpy()
         rel = np.linalg.norm(got - want, axis=0) / np.linalg.norm(want, axis=0)
         assert rel.max() < 1e-12, (call, rel.max())
+        exact = steps.shifted_solve(T, z, B, adjoint=adjoint)
+        rel = np.linalg.norm(got - exact, axis=0) / np.linalg.norm(exact, axis=0)
+        assert rel.max() < 1e-12, (call, rel.max())
     h.close()
 
 
@@ -73,4 +78,14 @@ def test_noalloc_rejects_oversized_calls():
                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == p._abi.ERR_ARG
     assert b"scratch" in lib.pseudo_last_error()
+    # a column count whose scratch size would overflow 64 bits is refused too,
+    # before any launch (X and z are never touched)
+    before = lib.pseudo_launch_count()
+    rc = lib.pseudo_solve_noalloc(h._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                  (1 << 60) + 1000, 0, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == p._abi.ERR_ARG and lib.pseudo_launch_count() == before
+    # a successful call clears the message of the failed one
+    rc = lib.pseudo_solve_noalloc(h._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(z.data_ptr()), 8, 0,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0 and lib.pseudo_last_error() == b""
     h.close()
