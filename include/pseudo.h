@@ -74,7 +74,10 @@ enum {
     PSEUDO_PT_REFINED = 2,       /* refined by LOBPCG-SVD / Lanczos */
     PSEUDO_PT_NOT_CONVERGED = 4, /* iteration cap hit; best estimate returned */
     PSEUDO_PT_IR_FALLBACK = 8,   /* mixed precision refinement fell back to FP64 */
-    PSEUDO_PT_SINGULAR = 16      /* z hit a diagonal entry of T to working precision */
+    PSEUDO_PT_SINGULAR = 16      /* sigma_min(T - zI) is below FP64 working precision (z on a
+                                    diagonal entry of T, or deep inside the pseudospectrum of a
+                                    strongly nonnormal T): sigma_out is an upper bound at the
+                                    rounding level and res_out = sigma_out / (||T||_2,est + |z|) */
 };
 
 /* Options; pseudo_opts_default() fills the paper's parameters (Sec. 4):
@@ -122,6 +125,7 @@ typedef struct {
     int64_t lobpcg_iters;
     int64_t n_fallback;  /* mixed precision: points redone in FP64 (PSEUDO_PT_IR_FALLBACK) */
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
+    int64_t n_singular;  /* of those, points found singular to working precision (PSEUDO_PT_SINGULAR) */
 } pseudo_stats_t;
 
 /* Per-kernel-class accounting (filled when pseudo_opts.profile = 1): launches,
@@ -279,6 +283,17 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
 int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pseudo_c64 *Y,
                   const pseudo_c64 *z, int64_t ncols, int adjoint, int subtract, int precision,
                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* pseudo_set_wait_limit: the limit, in nanoseconds, of every bounded wait of
+ * the tensor-core kernels of this handle (the mixed-precision solves and
+ * products; default 10^9 = 1 s).  A wait that runs out makes its kernel stop,
+ * let the copies and MMAs it has in flight finish, release its tensor memory
+ * and record the failure; the call then returns PSEUDO_ERR_TIMEOUT with its
+ * outputs invalid, and the handle stays usable.  0 makes any wait that is not
+ * already satisfied give up at once (for testing that path).  No
+ * counterpart in the paper: it is part of the library's failure handling.
+ * Errors: ARG (h NULL). */
+int pseudo_set_wait_limit(pseudo_handle h, uint64_t ns);
 
 /* pseudo_solve_noalloc: the FP64 form of pseudo_solve without a workspace, for
  * callers that cannot allocate device memory (a process that reserved its whole

@@ -97,6 +97,10 @@ class Pseudo:
     def reset_stats(self):
         check(self._lib.pseudo_stats_reset(self._h))
 
+    def set_wait_limit(self, ns: int):
+        """Limit of the bounded waits of the tensor-core kernels (pseudo_set_wait_limit)."""
+        check(self._lib.pseudo_set_wait_limit(self._h, ctypes.c_uint64(int(ns))))
+
     def workspace_bytes(self, npts: int, opts: Opts) -> int:
         b = ctypes.c_size_t()
         check(self._lib.pseudo_workspace_bytes(self._h, ctypes.byref(opts), int(npts), ctypes.byref(b)))

@@ -19,7 +19,7 @@ EXPORTED = (
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
     "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count", "pseudo_recycle_state_layout",
     "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch", "pseudo_matvec_workspace_bytes",
-    "pseudo_traversal_order",
+    "pseudo_traversal_order", "pseudo_set_wait_limit", "pseudo_solve_noalloc",
 )
 
 
@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "sv_R", "mv_M", "mv_M_fp64_refine", "n_points", "n_accepted", "n_refined", "n_not_converged",
         "n_updates", "lanczos_steps", "lobpcg_iters", "n_fallback")] + [(k, ctypes.c_double) for k in (
-        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")]
+        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")] + [("n_singular", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
     lib.pseudo_matvec_workspace_bytes.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_grid_batch_workspace_bytes.argtypes = [vp, ci, vp, po, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_grid_batch.argtypes = [vp, ci, vp, vp, vp, ci, po, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.pseudo_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
+    lib.pseudo_solve_noalloc.argtypes = [vp, vp, vp, i64, ci, vp]
     for name in EXPORTED:
         fn = getattr(lib, name)
         if name not in ("pseudo_destroy", "pseudo_last_error", "pseudo_launch_count"):

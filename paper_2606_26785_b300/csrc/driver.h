@@ -60,7 +60,8 @@ struct pseudo_ctx {
     // FP32 diagonal blocks of T and T^H; device error word of bounded waits
     float *tcA_U = nullptr, *tcA_L = nullptr;
     float2 *tcD_U = nullptr, *tcD_L = nullptr;
-    int *dev_err = nullptr;
+    int *dev_err = nullptr;                  // [0] a bounded wait gave up, [1] scratch flag of argument checks
+    uint64_t wait_ns = 1000000000ull;        // limit of every bounded wait in the tensor-core kernels
     // tensor-core double-single products: 7 bf16 slices of T and T^H per
     // (64-row tile, 16-column chunk) image, and the per-row scale exponents
     void *ozA_U = nullptr, *ozA_L = nullptr;
@@ -148,9 +149,10 @@ struct IRBufs {
 struct IRPlan {
     std::vector<int> cnt;  // cnt[it]: columns still refining at step it
 };
-// need[c] for c < sig.size(), zero for the other columns up to S_total
+// need[c] for c < sig.size(), zero for the other columns up to S_total and for
+// the columns marked in *skip (their solution stays zero)
 void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<double2> &z, int max_ir,
-             const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total = 0);
+             const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total = 0, const std::vector<char> *skip = nullptr);
 cudaError_t ir_solve_cols(pseudo_ctx *h, const IRBufs &b, int lower, const double2 *zc, int S, const double2 *B,
                           double2 *X, const IRPlan &plan, cudaStream_t s);
 }  // namespace pseudo

@@ -57,6 +57,9 @@ struct LancLayout {
 
 // Slots of the FP64 pass that mixed precision hands its hard points to.
 constexpr int FB_SLOTS = 256;
+// kappa * u above which a point goes to the FP64 pass: the planned refinement
+// would contract by less than 4 per step
+constexpr double FB_KU = 1.0 / 32.0;
 
 static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool fp32, int mmax) {
     int64_t S = o->shift_batch > 0 ? o->shift_batch : 8192;
@@ -161,11 +164,22 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
         {
             std::vector<double> th(P), sg(P);
             std::vector<double2> zh(P);
+            std::vector<int> cv(P);
+            std::vector<char> skip(P, 0);
             cudaMemcpyAsync(th.data(), L.fin_theta, P * sizeof(double), cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(zh.data(), L.fin_z, P * sizeof(double2), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(cv.data(), L.fin_conv, P * sizeof(int), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
-            for (int c = 0; c < P; ++c) sg[c] = th[c] > 0.0 ? 1.0 / std::sqrt(th[c]) : 0.0;
-            ir_plan(h, sg, zh, o->max_ir, ib, plan, s, F);
+            const double u = solve32_unit_roundoff(h);
+            for (int c = 0; c < P; ++c) {
+                sg[c] = th[c] > 0.0 ? 1.0 / std::sqrt(th[c]) : 0.0;
+                // points the FP64 pass will redo whatever the refinement gives
+                // (launch_fin_scatter's test with the Lanczos value, which bounds
+                // the refined one from above) are not refined
+                const double mz = h->norm2 + std::hypot(zh[c].x, zh[c].y);
+                skip[c] = !cv[c] || !(sg[c] > 0.0) || (mz / sg[c]) * u > FB_KU;
+            }
+            ir_plan(h, sg, zh, o->max_ir, ib, plan, s, F, &skip);
         }
         if ((e = ir_solve_cols(h, ib, 1, L.fin_z, F, L.Ufin, L.X64, plan, s)) != cudaSuccess) return cuda_err(e, "refine");
         cudaMemcpyAsync(L.B64, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
@@ -185,9 +199,110 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);
     // kappa * u above 1/32: the planned refinement contracts by less than 4 per step
     launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0, h->norm2, L.eps,
-                       neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), 1.0 / 32.0,
+                       neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), FB_KU,
                        L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;
+}
+
+// The points handed to the FP64 pass whose sigma_min lies below working
+// precision: one FP64 inverse-iteration step x = N(z)^{-1} v from the seeded
+// start vector v leaves ||(T - zI) x|| / ||x|| at the rounding level there.
+// Since sigma_min <= ||(T - zI) x|| for a unit x, a point whose computed
+// residual r is at most tau = 64 sqrt(n) eps (||T||_2 + |z|), with 2 tau below
+// every epsilon level, is finished with sigma = r (an upper bound of a value
+// no FP64 method resolves further), res = r / (||T||_2 + |z|) (the relative
+// backward error of x as a null vector), every membership bit set and the
+// PSEUDO_PT_SINGULAR flag; keep[t] = 0 marks it done, 1 sends it on to the
+// full FP64 inverse Lanczos.
+__global__ void deep_certify_kernel(int cnt, const int *__restrict__ list, const double2 *__restrict__ zc,
+                                    const double *__restrict__ r2, double norm2, double sqrt_n, const double *eps,
+                                    int neps, double min_level, double *__restrict__ sigma_out,
+                                    double *__restrict__ res_out, int32_t *__restrict__ flags_out,
+                                    uint32_t *__restrict__ member_out, int *__restrict__ keep) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cnt) return;
+    const double r = sqrt(fmax(r2[t], 0.0));
+    const double mz = norm2 + sqrt(zc[t].x * zc[t].x + zc[t].y * zc[t].y);
+    const double tau = 64.0 * sqrt_n * 2.220446049250313e-16 * mz;
+    keep[t] = 1;
+    if (!(r <= tau) || !(2.0 * tau < min_level)) return;
+    keep[t] = 0;
+    const int g = list[t];
+    sigma_out[g] = r;
+    if (res_out) res_out[g] = r / mz;
+    if (flags_out) flags_out[g] = PSEUDO_PT_REFINED | PSEUDO_PT_IR_FALLBACK | PSEUDO_PT_SINGULAR;
+    if (member_out) {
+        uint32_t m = 0;
+        for (int e = 0; e < neps; ++e) m |= (r < eps[e] ? 1u : 0u) << e;
+        member_out[g] = m;
+    }
+}
+
+// Triage of the nfb points in L.fb_list before the FP64 pass: the points
+// certified singular to working precision (deep_certify_kernel) are written
+// out; the others are compacted to the front of L.fb_list, in their order,
+// and nfb becomes their count.  Scratch: the main pass's Lanczos basis, free
+// by now.  Returns 0, or an error code.
+static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, LancLayout &Lfb, const double2 *zall,
+                           int neps, double min_level, double *sig_all, double *res_all, int32_t *flags_all,
+                           uint32_t *member_all, int &nfb, cudaStream_t s) {
+    const int n = h->n, n_pad = h->n_pad;
+    const size_t qbytes = (size_t)(L.mmax + 1) * n * L.S * (L.fp32 ? sizeof(float2) : sizeof(double2));
+    // per column: x, (T - zI) x, solve scratch, shift, norm, flag, list entry (+ slack for alignment)
+    const size_t per_col = 2 * (size_t)n * sizeof(double2) + (size_t)n_pad * sizeof(double2) + 64;
+    int64_t tc = std::min<int64_t>(nfb, (int64_t)(qbytes / per_col) - 64);
+    tc = tc / 8 * 8;
+    if (tc < 8) return 0;  // no room: every point takes the full FP64 pass
+    Carver c((char *)L.Q, qbytes);
+    double2 *X = c.get<double2>((size_t)n * tc), *Y = c.get<double2>((size_t)n * tc);
+    double2 *xs = (double2 *)c.take(trsv_scratch_bytes(0, n_pad, tc));
+    double2 *zc = c.get<double2>(tc);
+    double *r2 = c.get<double>(tc);
+    int *keep = c.get<int>(tc);
+    if (c.overflow) return 0;
+    std::vector<int> list_h(nfb), keep_h(tc), kept;
+    kept.reserve(nfb);
+    cudaMemcpyAsync(list_h.data(), L.fb_list, nfb * sizeof(int), cudaMemcpyDeviceToHost, s);
+    launch_start_vector(Lfb.startv, n, o->seed, s);
+    cudaError_t e = cudaSuccess;
+    int64_t nsing = 0;
+    for (int off = 0; off < nfb; off += (int)tc) {
+        const int cnt = (int)std::min<int64_t>(tc, nfb - off);
+        launch_fb_gather(L.fb_list + off, cnt, zall, zc, s);
+        launch_bcast_start<double>(Lfb.startv, n, cnt, X, s);
+        int k0 = kp_begin(h, s);
+        e = launch_trsv64(h->L64, n, n_pad, 1, nullptr, zc, cnt, nullptr, X, cnt, xs, s);
+        kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, cnt), tri_bytes(n, cnt, 16, 16, 2), s);
+        if (e != cudaSuccess) return cuda_err(e, "fallback triage");
+        launch_normalize(X, n, cnt, nullptr, s);
+        k0 = kp_begin(h, s);
+        e = launch_trsv64(h->U64, n, n_pad, 0, nullptr, zc, cnt, nullptr, X, cnt, xs, s);
+        kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, cnt), tri_bytes(n, cnt, 16, 16, 2), s);
+        if (e != cudaSuccess) return cuda_err(e, "fallback triage");
+        launch_normalize(X, n, cnt, nullptr, s);
+        k0 = kp_begin(h, s);
+        e = launch_trmv64(h->U64, n, n_pad, 0, nullptr, zc, cnt, nullptr, X, cnt, nullptr, cnt, Y, cnt, 0, s);
+        kp_end(h, k0, PSEUDO_K_TRMV64, tri_flops(n, cnt), tri_bytes(n, cnt, 16, 16, 2), s);
+        if (e != cudaSuccess) return cuda_err(e, "fallback triage");
+        launch_colnorm2(Y, n, cnt, nullptr, r2, s);
+        note_launch();
+        deep_certify_kernel<<<(cnt + 127) / 128, 128, 0, s>>>(cnt, L.fb_list + off, zc, r2, h->norm2,
+                                                              std::sqrt((double)n), L.eps, neps, min_level, sig_all,
+                                                              res_all, flags_all, member_all, keep);
+        cudaMemcpyAsync(keep_h.data(), keep, cnt * sizeof(int), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback triage");
+        for (int t = 0; t < cnt; ++t) {
+            if (keep_h[t]) kept.push_back(list_h[off + t]);
+            else ++nsing;
+        }
+        h->stats.sv_R += 2 * (int64_t)cnt;
+        h->stats.mv_M_fp64_refine += cnt;
+    }
+    if (!kept.empty()) cudaMemcpyAsync(L.fb_list, kept.data(), kept.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback triage");
+    nfb = (int)kept.size();
+    h->stats.n_singular += nsing;
+    return 0;
 }
 
 // Continuous-batching Lanczos over the npts points zall (device) with the
@@ -308,7 +423,15 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     cudaMemcpyAsync(&nbad, L.nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (mixed) cudaMemcpyAsync(&nfb, L.fb_cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "pseudo_grid");
-    // the points mixed precision could not vouch for, in FP64, CH at a time
+    h->stats.n_fallback += nfb;
+    // the points mixed precision could not vouch for: first those singular to
+    // working precision, then the rest in FP64 inverse Lanczos, CH at a time
+    if (nfb > 0) {
+        double min_level = HUGE_VAL;
+        for (int i = 0; i < io.neps; ++i) min_level = std::min(min_level, io.eps_host[i]);
+        rc = fallback_triage(h, o, L, Lfb, zall, io.neps, min_level, sig_all, res_all, flags_all, member_all, nfb, s);
+        if (rc < 0) return rc;
+    }
     for (int off = 0; off < nfb; off += L.CH) {
         const int cnt = std::min(L.CH, nfb - off);
         if (io.neps > 0) cudaMemcpyAsync(Lfb.eps, L.eps, io.neps * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -322,7 +445,6 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback");
         nbad += nb;
     }
-    h->stats.n_fallback += nfb;
     if (io.on_host) {
         cudaMemcpyAsync(io.sigma, sig_all, npts * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (io.res) cudaMemcpyAsync(io.res, res_all, npts * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -112,12 +112,12 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaMalloc(&h->tcA_L, tc_pack_floats(h->n_pad) * sizeof(float) + 16)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcA_L"));
     if ((e = cudaMalloc(&h->tcD_U, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_U"));
     if ((e = cudaMalloc(&h->tcD_L, tc_diag_elems(h->n_pad) * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc tcD_L"));
-    if ((e = cudaMalloc(&h->dev_err, sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc dev_err"));
+    if ((e = cudaMalloc(&h->dev_err, 2 * sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc dev_err"));
     if ((e = cudaMalloc(&h->ozA_U, oz_a_elems(h->n_pad) * 2 + 256)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozA_U"));
     if ((e = cudaMalloc(&h->ozA_L, oz_a_elems(h->n_pad) * 2 + 256)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozA_L"));
     if ((e = cudaMalloc(&h->ozE_U, h->n_pad * sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozE_U"));
     if ((e = cudaMalloc(&h->ozE_L, h->n_pad * sizeof(int))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc ozE_L"));
-    if ((e = cudaMemsetAsync(h->dev_err, 0, sizeof(int), s)) != cudaSuccess) return fail(cuda_err(e, "memset"));
+    if ((e = cudaMemsetAsync(h->dev_err, 0, 2 * sizeof(int), s)) != cudaSuccess) return fail(cuda_err(e, "memset"));
     if ((e = cudaMalloc(&bad, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if ((e = cudaMalloc(&dsum, 64)) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
     if (t_on_host) {
@@ -173,6 +173,13 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(e, "create"));
     memset(&h->stats, 0, sizeof h->stats);
     *out = h;
+    return PSEUDO_OK;
+}
+
+int pseudo_set_wait_limit(pseudo_handle h, uint64_t ns) {
+    clear_err();
+    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
+    h->wait_ns = ns;
     return PSEUDO_OK;
 }
 
@@ -380,6 +387,16 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     if (o->io_host) {
         for (int64_t i = 0; i < npts; ++i)
             if (!std::isfinite(z[i].re) || !std::isfinite(z[i].im)) return set_err(PSEUDO_ERR_NONFINITE, "z[%lld] is not finite", (long long)i);
+    } else {
+        // device shifts: one pass over z before any other work
+        cudaStream_t s0 = (cudaStream_t)stream;
+        int zbad = 0;
+        cudaMemsetAsync(h->dev_err + 1, 0, sizeof(int), s0);
+        launch_nonfinite((const double2 *)z, npts, h->dev_err + 1, s0);
+        cudaMemcpyAsync(&zbad, h->dev_err + 1, sizeof(int), cudaMemcpyDeviceToHost, s0);
+        const cudaError_t ez = cudaStreamSynchronize(s0);
+        if (ez != cudaSuccess) return cuda_err(ez, "checking z");
+        if (zbad) return set_err(PSEUDO_ERR_NONFINITE, "z has non-finite entries");
     }
     size_t need = 0;
     pseudo_workspace_bytes(h, o, npts, &need);

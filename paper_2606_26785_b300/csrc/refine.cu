@@ -23,7 +23,7 @@ __global__ void need_mask_kernel(const int *__restrict__ need, int it, int S, in
 }
 
 void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<double2> &z, int max_ir,
-             const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total) {
+             const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total, const std::vector<char> *skip) {
     const int S = (int)sig.size();
     if (S_total < S) S_total = S;
     std::vector<int> need(S_total, 0), perm(S);
@@ -40,6 +40,7 @@ void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<do
         const double target = std::max(1e-15, std::min(1e-8, 1e-5 * sg / mz));
         int k = (int)std::ceil(std::log(target) / std::log(rho));
         need[c] = std::max(2, std::min(max_ir, k));
+        if (skip && (*skip)[c]) need[c] = 0;
     }
     std::iota(perm.begin(), perm.end(), 0);
     std::stable_sort(perm.begin(), perm.end(), [&](int a, int c) { return need[a] > need[c]; });

@@ -273,7 +273,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                const int *__restrict__ fx, int n, int n_pad, int lower, const int *__restrict__ cols,
                const double2 *__restrict__ zc, int ncols, const double2 *__restrict__ X, int64_t ldx,
                const double2 *__restrict__ B, int64_t ldb, double2 *__restrict__ Y, int64_t ldy, int subtract,
-               int *err) {
+               int *err, uint64_t wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_ld[OZ_NSTG], bar_mma[OZ_NSTG];
     __shared__ uint32_t s_tmem;
@@ -331,7 +331,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     for (int q = 0; q < nch; ++q) {
         const int st = q % OZ_NSTG;
         if (tid == 0 && !s_abort) {
-            if (!tc::mbar_wait(&bar_ld[st], (q / OZ_NSTG) & 1)) {
+            if (!tc::mbar_wait(&bar_ld[st], (q / OZ_NSTG) & 1, wait_ns)) {
                 s_abort = 1;
             } else {
                 tc::tc_fence_after();
@@ -355,7 +355,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
                 mma_last = q;
                 const int qn = q + OZ_NSTG - 1;
                 if (qn < nch) {
-                    if (q >= 1 && !tc::mbar_wait(&bar_mma[(q - 1) % OZ_NSTG], ((q - 1) / OZ_NSTG) & 1)) {
+                    if (q >= 1 && !tc::mbar_wait(&bar_mma[(q - 1) % OZ_NSTG], ((q - 1) / OZ_NSTG) & 1, wait_ns)) {
                         s_abort = 1;
                     } else {
                         issue_load(qn);
@@ -366,7 +366,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
         }
         // end of an exact segment: fold the level sums into the double-single totals
         if ((q % OZ_SEG) == OZ_SEG - 1 || q == nch - 1) {
-            if (tid == 0 && !s_abort && !tc::mbar_wait(&bar_mma[st], (q / OZ_NSTG) & 1)) s_abort = 1;
+            if (tid == 0 && !s_abort && !tc::mbar_wait(&bar_mma[st], (q / OZ_NSTG) & 1, wait_ns)) s_abort = 1;
             __syncthreads();
             if (s_abort) break;
             tc::tc_fence_after();
@@ -422,7 +422,11 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
         }
     }
     if (tid == 0 && s_abort) {
-        if (ld_pending >= 0) tc::mbar_wait(&bar_ld[ld_pending % OZ_NSTG], (ld_pending / OZ_NSTG) & 1, 100000000ull);
+        // loads run at most OZ_NSTG - 1 chunks ahead of the MMAs and a stage is
+        // reloaded only after its MMAs are done: every copy still in flight is
+        // one of the last OZ_NSTG - 1 issued, on a stage not re-armed since
+        for (int q = ld_pending - OZ_NSTG + 2 < 0 ? 0 : ld_pending - OZ_NSTG + 2; q <= ld_pending; ++q)
+            tc::mbar_wait(&bar_ld[q % OZ_NSTG], (q / OZ_NSTG) & 1, 100000000ull);
         if (mma_last >= 0) tc::mbar_wait(&bar_mma[mma_last % OZ_NSTG], (mma_last / OZ_NSTG) & 1, 100000000ull);
         atomicExch(err, 1);
     }
@@ -452,7 +456,7 @@ cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, cons
     note_launch();
     trmv_oz_kernel<<<grid, OZ_TH, OzSmem::bytes, s>>>((const __nv_bfloat16 *)(lower ? h->ozA_L : h->ozA_U), lower ? h->ozE_L : h->ozE_U, img, fx,
                                                       n, n_pad, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy,
-                                                      subtract, h->dev_err);
+                                                      subtract, h->dev_err, h->wait_ns);
     return cudaGetLastError();
 }
 

@@ -142,14 +142,15 @@ __device__ __forceinline__ void named_bar(int id, int count) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
-// bounded wait that also gives up as soon as another role has aborted
-__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort) {
+// bounded wait (limit_ns) that also gives up as soon as another role has aborted
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                              uint64_t limit_ns) {
     if (tc::mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = tc::global_ns();
     for (;;) {
         if (tc::mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
-        if (tc::global_ns() - t0 > 1000000000ull) { *abort = 1; return false; }
+        if (tc::global_ns() - t0 > limit_ns) { *abort = 1; return false; }
     }
 }
 }  // namespace
@@ -182,7 +183,8 @@ template <int NC>
 __global__ void __launch_bounds__(TC_THREADS, TC_NS <= 2 ? 2 : 1)
 trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
-               const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err) {
+               const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err,
+               uint64_t wait_ns) {
     using L = TcSmem<NC>;
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
@@ -248,10 +250,10 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                     const int k0 = lower ? KC * t : n_pad - KC * (t + 1);
                     const int pk = lower ? k0 / MB : P - 1 - k0 / MB;  // processing index of those rows' panel
                     if (pk >= known) {
-                        if (!wait_or_abort(&solved, pk & 1, &s_abort)) { ok = false; break; }
+                        if (!wait_or_abort(&solved, pk & 1, &s_abort, wait_ns)) { ok = false; break; }
                         known = pk + 1;
                     }
-                    if (q >= NS && !wait_or_abort(&freeb[st], ((q / NS) - 1) & 1, &s_abort)) { ok = false; break; }
+                    if (q >= NS && !wait_or_abort(&freeb[st], ((q / NS) - 1) & 1, &s_abort, wait_ns)) { ok = false; break; }
                     float *dst = sbuf + st * STAGE_F;
                     tc::mbar_expect_tx(&full[st], (uint32_t)L::stage);
                     tc::bulk_g2s_hint(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st], keep);
@@ -270,14 +272,14 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
             int q = 0;
             for (int p = 0; p < P && !s_abort; ++p) {
                 const int buf = p & 1;
-                if (p >= 2 && !wait_or_abort(&acc_free[buf], ((p >> 1) - 1) & 1, &s_abort)) break;
+                if (p >= 2 && !wait_or_abort(&acc_free[buf], ((p >> 1) - 1) & 1, &s_abort, wait_ns)) break;
                 tc::tc_fence_after();
                 const uint32_t dacc = tmem + buf * (TC_NACC * NR);
                 const int nch = 8 * p;
                 bool ok = true;
                 for (int t = 0; t < nch; ++t, ++q) {
                     const int st = q % NS;
-                    if (!wait_or_abort(&full[st], (q / NS) & 1, &s_abort)) { ok = false; break; }
+                    if (!wait_or_abort(&full[st], (q / NS) & 1, &s_abort, wait_ns)) { ok = false; break; }
                     tc::tc_fence_after();
                     const uint32_t ah = s0 + st * (STAGE_F * 4), al = ah + A_SPLIT * 4;
                     const uint32_t bh = ah + A_CHUNK * 4, bl = bh + L::B_SPLIT * 4;
@@ -318,7 +320,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
         for (int p = 0; p < P; ++p) {
             const int J = lower ? p : P - 1 - p;
             const int buf = p & 1;
-            if (i == 0) s_flag_diag = wait_or_abort(&acc_full[buf], (p >> 1) & 1, &s_abort) ? 1 : 0;
+            if (i == 0) s_flag_diag = wait_or_abort(&acc_full[buf], (p >> 1) & 1, &s_abort, wait_ns) ? 1 : 0;
             named_bar(BAR_DIAG, 128);
             if (!s_flag_diag) break;
             tc::tc_fence_after();
@@ -436,8 +438,12 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
     // ---- teardown (also after an abort: let copies and MMAs in flight finish)
     __syncthreads();
     if (tid == 0 && s_abort) {
+        // copies still in flight are among the last NS issued (a stage is
+        // reloaded only after its MMAs are done); none of those stages has been
+        // re-armed since, so each wait below ends when its copy lands
         const int ql = s_last_ld, qm = s_last_mma;
-        if (ql >= 0) tc::mbar_wait(&full[ql % NS], (ql / NS) & 1, 100000000ull);
+        for (int q = ql - NS + 1 < 0 ? 0 : ql - NS + 1; q <= ql; ++q)
+            tc::mbar_wait(&full[q % NS], (q / NS) & 1, 100000000ull);
         if (qm >= 0) tc::mbar_wait(&freeb[qm % NS], (qm / NS) & 1, 100000000ull);
         atomicExch(err, 1);
     }
@@ -460,7 +466,7 @@ cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, cons
     note_launch();
     trsv_tc_kernel<NC_TC><<<grid, TC_THREADS, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
                                                       h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs,
-                                                      h->dev_err);
+                                                      h->dev_err, h->wait_ns);
     return cudaGetLastError();
 }
 
