@@ -60,6 +60,8 @@ enum { PSEUDO_INVLANC = 0, PSEUDO_RECYCLE = 1 };
 enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
 /* pseudo_solve / pseudo_matvec only: the CUDA-core kernels instead of the tensor-core ones */
 enum { PSEUDO_MIXED_CUDACORE = 2 };
+/* pseudo_solve only: the solve in double-single arithmetic on the FP32 units */
+enum { PSEUDO_DOUBLE_SINGLE = 3 };
 
 /* grid traversal of the recycling path (pseudo_opts.traversal):
  * BATCH_ZIGZAG = the batch-zigzag order of Sec. 2.3 with column batches of
@@ -73,7 +75,8 @@ enum {
     PSEUDO_PT_ACCEPTED = 1,      /* recycled Ritz value accepted (no refinement) */
     PSEUDO_PT_REFINED = 2,       /* refined by LOBPCG-SVD / Lanczos */
     PSEUDO_PT_NOT_CONVERGED = 4, /* iteration cap hit; best estimate returned */
-    PSEUDO_PT_IR_FALLBACK = 8,   /* mixed precision refinement fell back to FP64 */
+    PSEUDO_PT_IR_FALLBACK = 8,   /* mixed precision: kappa too large for the FP32 solves; the
+                                    point was redone with double-single (about 2^-46) solves */
     PSEUDO_PT_SINGULAR = 16      /* sigma_min(T - zI) is below FP64 working precision (z on a
                                     diagonal entry of T, or deep inside the pseudospectrum of a
                                     strongly nonnormal T): sigma_out is an upper bound at the
@@ -123,9 +126,12 @@ typedef struct {
     int64_t n_updates;   /* updateRecy calls */
     int64_t lanczos_steps;
     int64_t lobpcg_iters;
-    int64_t n_fallback;  /* mixed precision: points redone in FP64 (PSEUDO_PT_IR_FALLBACK) */
+    int64_t n_fallback;  /* mixed precision: points redone with double-single solves
+                            (PSEUDO_PT_IR_FALLBACK) */
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
     int64_t n_singular;  /* of those, points found singular to working precision (PSEUDO_PT_SINGULAR) */
+    int64_t n_rtilde_capped; /* recycle mode: recySing evaluations whose r~ of eq. (tau) exceeded the
+                                16 columns the second Rayleigh--Ritz step keeps */
 } pseudo_stats_t;
 
 /* Per-kernel-class accounting (filled when pseudo_opts.profile = 1): launches,
@@ -140,6 +146,7 @@ enum {
     PSEUDO_K_TRMV_DS,     /* triangular product / residual, double-single on FP32 units */
     PSEUDO_K_RECYSING,    /* recycled Rayleigh--Ritz-SVD + residual, one CTA per point */
     PSEUDO_K_LANCZOS,     /* Lanczos reorthogonalisation */
+    PSEUDO_K_TRSV_DS,     /* multi-shift triangular solve, double-single on FP32 units */
     PSEUDO_K_COUNT
 };
 typedef struct {
@@ -263,7 +270,10 @@ int64_t pseudo_launch_count(void);
  *               (Alg. 3, lobpcgSvd on R(z)^{-*}; sv_R in Table 2).
  *   X   : device, row-major n x ncols complex (element (i, c) at X[i*ncols + c]).
  *   z   : device, ncols complex shifts, one per column.
- *   precision : PSEUDO_FP64 (all FP64) or PSEUDO_MIXED (FP32 arithmetic).
+ *   precision : PSEUDO_FP64 (all FP64), PSEUDO_MIXED (FP32 arithmetic on the tensor
+ *               cores), PSEUDO_MIXED_CUDACORE (FP32 on the CUDA cores) or
+ *               PSEUDO_DOUBLE_SINGLE (double-single arithmetic on the CUDA cores,
+ *               about 2^-46 relative per operation).
  *   workspace : device, >= pseudo_solve_workspace_bytes bytes.
  * pseudo_matvec: Y[:, c] <- B[:, c] - (T - z_c I)^{op} X[:, c] (subtract = 1) or
  *   Y[:, c] <- (T - z_c I)^{op} X[:, c] (subtract = 0, B ignored and may be NULL); the

@@ -12,10 +12,11 @@ import numpy as np
 
 from . import _abi
 from ._abi import (  # noqa: F401
-    FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON, Opts,
+    DOUBLE_SINGLE, FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON, Opts,
     PseudoError, Stats, check)
 
-__all__ = ["Pseudo", "grid_batch", "traversal_order", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE", "INVLANC",
+__all__ = ["Pseudo", "grid_batch", "traversal_order", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE",
+           "DOUBLE_SINGLE", "INVLANC",
            "RECYCLE", "TRAVERSE_BATCH_ZIGZAG", "TRAVERSE_HILBERT", "TRAVERSE_MORTON", "PseudoError"]
 
 

@@ -10,7 +10,7 @@ OK = 0
 WARN_NOT_CONVERGED = 1
 ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 INVLANC, RECYCLE = 0, 1
-FP64, MIXED, MIXED_CUDACORE = 0, 1, 2
+FP64, MIXED, MIXED_CUDACORE, DOUBLE_SINGLE = 0, 1, 2, 3
 TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON = 0, 1, 2
 PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4, 8, 16
 
@@ -40,14 +40,14 @@ class KStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos")
+KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos", "trsv_ds")
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "sv_R", "mv_M", "mv_M_fp64_refine", "n_points", "n_accepted", "n_refined", "n_not_converged",
         "n_updates", "lanczos_steps", "lobpcg_iters", "n_fallback")] + [(k, ctypes.c_double) for k in (
-        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")] + [("n_singular", ctypes.c_int64)]
+        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")] + [("n_singular", ctypes.c_int64), ("n_rtilde_capped", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -46,6 +46,11 @@ cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const doubl
                     const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
 // unit roundoff of the FP32 solve in use (for the refinement plan)
 double solve32_unit_roundoff(const pseudo_ctx *h);
+// trsv_ds.cu: the multi-shift solve in double-single arithmetic (X is FP64 in
+// and out; xs is trsv_ds_scratch_bytes(n_pad, ncols) of scratch)
+size_t trsv_ds_scratch_bytes(int64_t n_pad, int64_t ncols);
+cudaError_t launch_trsv_ds(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                           const int *ncols_dev, double2 *X, int64_t ldx, void *xs, cudaStream_t s);
 // trmv_oz.cu: double-single-accurate shifted products on the tensor cores
 int64_t oz_a_elems(int n_pad);
 size_t oz_scratch_bytes(int n_pad, int64_t ncols);

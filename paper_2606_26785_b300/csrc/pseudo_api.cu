@@ -260,7 +260,8 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
                  void *workspace, size_t workspace_bytes, void *stream) {
     clear_err();
     if (!h || !X || !z || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
-    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE)
+    if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE &&
+        precision != PSEUDO_DOUBLE_SINGLE)
         return set_err(PSEUDO_ERR_ARG, "bad precision");
     if (ncols == 0) return PSEUDO_OK;
     size_t need = 0;
@@ -274,6 +275,9 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
         double2 *xs = (double2 *)c.take(trsv_scratch_bytes(0, h->n_pad, ncols));
         e = launch_trsv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, nullptr, (const double2 *)z, (int)ncols,
                           nullptr, (double2 *)X, ncols, xs, s);
+    } else if (precision == PSEUDO_DOUBLE_SINGLE) {
+        void *xs = c.take(trsv_ds_scratch_bytes(h->n_pad, ncols));
+        e = launch_trsv_ds(h, lower, nullptr, (const double2 *)z, (int)ncols, nullptr, (double2 *)X, ncols, xs, s);
     } else {
         float2 *xs = (float2 *)c.take(trsv_scratch_bytes(1, h->n_pad, ncols));
         float2 *X32 = (float2 *)c.take((size_t)h->n * ncols * sizeof(float2));

@@ -683,7 +683,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     const double eps_shift = o->eps_shift_rel * h->norm2 * h->norm2;
     const bool trace = getenv("PSEUDO_TRACE") != nullptr;  // per-round progress on stderr
     int64_t n_acc = 0, n_ref = 0;
-    std::vector<int> gidx_r, lane_r, acc_h, items_h;
+    std::vector<int> gidx_r, lane_r, acc_h, rt_h, items_h;
     for (int round = 0;; ++round) {
         gidx_r.clear();
         lane_r.clear();
@@ -717,8 +717,11 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             if (e != cudaSuccess) return cuda_err(e, "recySing");
         }
         acc_h.assign(np, 0);
+        rt_h.assign(np, 0);
         cudaMemcpyAsync(acc_h.data(), R.acc_r, np * sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(rt_h.data(), R.rt_r, np * sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "recySing");
+        for (int j = 0; j < np; ++j) h->stats.n_rtilde_capped += rt_h[j] > RTMAX ? 1 : 0;
         note_launch(); scatter_round_kernel<<<(np + 127) / 128, 128, 0, s>>>(nullptr, np, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_ACCEPTED,
                                                               R.eps, io.neps, sig_all, res_all, flags_all, member_all,
                                                               nullptr);

@@ -6,7 +6,11 @@
 //   1. H(z) = H1 - z H2 - conj(z) H2^H + (|z|^2 + eps) I      (eq. (rayleighN))
 //      and its eigenpairs (Theta ascending, G)                  (eq. (step1))
 //   2. r~ = smallest j >= r with theta_{j+1} - theta_j > theta_k eps_m / tau
-//                                                                (eq. (tau))
+//      (eq. (tau)), then capped at RTMAX columns: the Ritz pairs come from
+//      the span of V G_{1:min(r~, RTMAX)}, a subspace of span V, so they stay
+//      upper bounds and the acceptance test below judges the pair actually
+//      returned; the cap can only cost acceptances.  rt_out gets the
+//      uncapped r~.
 //   3. Y = (W1 - z V) G_{1:r~}; R~ from the Gram Y^H Y by a column-scaled
 //      Cholesky (Y's columns are orthogonal up to rounding, so the scaled
 //      Gram is close to I and the factor keeps full relative accuracy);
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(RS_THREADS) recysing_kernel(RecySingArgs a) {
     double *rot = theta + KM;             // 224 doubles
     double *sig = rot + 224;              // RTMAX
     int *perm = (int *)(sig + RTMAX);     // KM
-    __shared__ int s_rt, s_ok;
+    __shared__ int s_rt, s_ok, s_rt_rule;
     __shared__ double s_w[2][RS_THREADS / 32];
 
     const int64_t ldv = a.ldv;
@@ -98,6 +102,7 @@ __global__ void __launch_bounds__(RS_THREADS) recysing_kernel(RecySingArgs a) {
         const double thr = theta[k - 1] * 2.220446049250313e-16 / a.tau;
         for (int jj = a.r; jj < k; ++jj)
             if (fabs(theta[jj - 1] - theta[jj]) > thr) { rt = jj; break; }
+        s_rt_rule = rt;  // reported: r~ of eq. (tau) before the cap
         if (rt > RTMAX) rt = RTMAX;
         if (rt > k) rt = k;
         s_rt = rt;
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(RS_THREADS) recysing_kernel(RecySingArgs a) {
         a.sigma[j] = xi1;
         a.res[j] = xi1 > 0.0 ? nw1 / (xi1 * Mz) : 1e300;
         a.accept[j] = acc ? 1 : 0;
-        a.rt[j] = rt;
+        a.rt[j] = s_rt_rule;
         a.xi2[j] = xi2v;
         a.w2[j] = nw2;
     }

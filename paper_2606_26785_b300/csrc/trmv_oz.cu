@@ -45,6 +45,9 @@ constexpr int OZ_A_SLICE = OZ_MR * OZ_KR;            // bf16 elements
 constexpr int OZ_B_SLICE = OZ_NC * OZ_KR;
 constexpr int OZ_A_IMG = OZ_NS * OZ_A_SLICE;         // 14336 elements, 28 KB
 constexpr int OZ_B_IMG = OZ_NS * OZ_B_SLICE;         // 7168 elements, 14 KB
+#ifndef OZ_GR
+#define OZ_GR 8  // row tiles per group of the tile order (see trmv_oz_kernel)
+#endif
 constexpr int OZ_TH = 256;  // two warpgroups: each TMEM lane quarter is read by two warps,
                              // one per half of the output columns
 
@@ -280,9 +283,19 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int NT = n_pad / OZ_CR;
-    const int ct = blockIdx.x;
-    // heaviest row tiles first: upper products are longest at the top
-    const int I = lower ? NT - 1 - (int)blockIdx.y : (int)blockIdx.y;
+    // Tile order: groups of OZ_GR row tiles, column tiles outer and row tiles
+    // inner within a group, so that the CTAs resident at one time share a few
+    // A slice streams (row tiles) and a few X slice streams (column tiles) in
+    // L2 instead of every CTA of a row tile streaming its own X slices from
+    // DRAM; groups run heaviest first (upper products are longest at the top).
+    const int tiles = (ncols + OZ_NC - 1) / OZ_NC;
+    const int64_t lin = blockIdx.x;
+    const int64_t grp = lin / ((int64_t)OZ_GR * tiles);
+    const int rows_in = min(OZ_GR, NT - (int)grp * OZ_GR);
+    const int64_t w_in = lin - grp * OZ_GR * tiles;
+    const int iy = (int)grp * OZ_GR + (int)(w_in % rows_in);
+    const int ct = (int)(w_in / rows_in);
+    const int I = lower ? NT - 1 - iy : iy;
     int c0, c1;
     chunk_range(I, n_pad, lower, c0, c1);
     const int nch = c1 - c0;
@@ -452,7 +465,7 @@ cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, cons
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     note_launch(); oz_slice_b_kernel<<<nsm * 8, 256, 0, s>>>(X, n, n_pad, ldx, cols, ncols, fx, img);
-    dim3 grid((unsigned)tiles, (unsigned)(n_pad / OZ_CR));
+    const unsigned grid = (unsigned)(tiles * (n_pad / OZ_CR));
     note_launch();
     trmv_oz_kernel<<<grid, OZ_TH, OzSmem::bytes, s>>>((const __nv_bfloat16 *)(lower ? h->ozA_L : h->ozA_U), lower ? h->ozE_L : h->ozE_U, img, fx,
                                                       n, n_pad, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy,

@@ -62,7 +62,7 @@ def test_triangular8000_mixed_matches_fp64():
     h.close()
 
 
-@pytest.mark.parametrize("mode,k", [("recycle", 8), ("recycle", 32), ("invlanc", 0)])
+@pytest.mark.parametrize("mode,k", [("recycle", 8), ("recycle", 32), ("recycle", 64), ("invlanc", 0)])
 def test_toeplitz1200_mixed(mode, k):
     """The banded Toeplitz + noise workload, reduced to n = 1200 on a 50 x 50
     grid over the full-size window, in mixed precision: the recycling path with
@@ -72,7 +72,11 @@ def test_toeplitz1200_mixed(mode, k):
     smallest singular values of a large banded Toeplitz matrix crowd together,
     so at some points the iteration caps (64 Lanczos steps, 60 LOBPCG
     iterations) cannot separate sigma_min from its neighbours: those points must
-    be reported as not converged, with an upper bound within 1e-3."""
+    be reported as not converged, with an upper bound within 1e-3.  At k = 64
+    the second Rayleigh--Ritz step keeps at most 16 of the r~ columns eq. (tau)
+    asks for; how often that cap binds is printed (it costs acceptances, not
+    accuracy: the returned pair comes from a subspace of span V and passes the
+    same acceptance test)."""
     import paper_2606_26785_b300 as p
 
     g = json.loads((GOLD / "toeplitz1200_samples.json").read_text())

@@ -69,6 +69,30 @@ def test_solve_fp32_tensor_cores(n, ncols, adjoint):
     assert errs[p.MIXED] < 30 * errs[p.MIXED_CUDACORE] + 1e-6, errs
 
 
+@pytest.mark.parametrize("n", [1, 2, 63, 64, 65, 300, 520])
+@pytest.mark.parametrize("ncols", [1, 7, 37, 300, 333])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_solve_double_single(n, ncols, adjoint):
+    """The double-single solve (FP32 pairs on the CUDA cores, the solve of the
+    points the FP32 solves cannot serve) against the oracle's substitution:
+    about 2^-46 relative per operation, so within 1e-12 on these
+    well-conditioned shifts, across ragged 64-row panels and both the narrow
+    (up to 296 columns) and the 8-column groups."""
+    import torch
+
+    import paper_2606_26785_b300 as p
+
+    T, z, B = _case(n, ncols, 3000 + 1000 * n + ncols)
+    h = p.Pseudo(T)
+    ref = steps.shifted_solve(T, z, B, adjoint)
+    X = torch.from_numpy(B.copy()).cuda()
+    h.solve(X, z, adjoint=adjoint, precision=p.DOUBLE_SINGLE)
+    got = X.cpu().numpy()
+    rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    h.close()
+    assert rel.max() < 1e-12, rel.max()
+
+
 @pytest.mark.parametrize("n", [1, 3, 65, 130])
 @pytest.mark.parametrize("adjoint", [False, True])
 def test_matvec_fp64(n, adjoint):

@@ -49,6 +49,23 @@ def test_grcar_recycle_full_grid(grcar, precision, rtol):
     assert st["mv_M"] == 3 * 4 * st["n_updates"]
 
 
+@pytest.mark.parametrize("traversal", [1, 2])
+@pytest.mark.parametrize("precision,rtol", [(0, 1e-10), (1, 1e-8)])
+def test_grcar_recycle_hilbert_morton(grcar, traversal, precision, rtol):
+    """The Hilbert (1) and Morton (2) grid orders that Sec. 5 names, on the
+    full Grcar grid, every point against the oracle; the acceptance count of
+    each order is printed (the recycled subspace follows the visiting order)."""
+    W, ref, off = grcar
+    out, st = _run(W, precision, rtol, traversal=traversal, lanes=1)
+    rep = check_sigma(out["sigma"], ref, n=W.n, fro=np.linalg.norm(W.C), schur_err=W.schur_err, oracle_off=off,
+                      rtol=rtol, eps_levels=EPS, member=out["member"])
+    print("traversal", traversal, "precision", precision, "accepted", st["n_accepted"], "of", W.z.size, rep)
+    assert rep["n_bad"] == 0, rep
+    assert rep["member_mismatch"] == 0, rep
+    assert st["n_accepted"] + st["n_refined"] == W.z.size
+    assert st["mv_M"] == 3 * 4 * st["n_updates"]
+
+
 def test_full_basis_makes_ritz_exact():
     # n = 8, r = 4, p_max = 2 -> k = 8 = n once two blocks are recycled
     rng = np.random.default_rng(5)
