@@ -55,6 +55,15 @@ WORKLOADS = {
 ORACLE_ROUNDS_SAMPLE = 96
 
 
+T_START = time.time()
+
+
+def log(msg):
+    """Progress on stderr (the JSON result line goes to stdout)."""
+    sys.stderr.write(f"[bench {time.time() - T_START:7.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
 def _peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -307,16 +316,23 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison paths and the CPU baseline")
+    ap.add_argument("--extras-budget", type=float, default=480.0,
+                    help="seconds of wall time the comparison paths may take; the ones that would start later are "
+                         "reported as skipped")
     ap.add_argument("--accuracy-full", action="store_true",
                     help="also run the FP64 path on every grid point and compare (about ten minutes at n = 8000)")
-    ap.add_argument("--profile-kernel", choices=["solve", "product"],
-                    help="for kernel profilers: 3 warm-up calls then 1 timed call of the tensor-core solve or the "
-                         "tensor-core double-single-accurate product on --profile-columns columns of the matrix")
+    ap.add_argument("--profile-kernel", choices=["solve", "product", "solve_ds", "solve_fp64"],
+                    help="for kernel profilers: 3 warm-up calls then 1 timed call of the tensor-core solve, the "
+                         "tensor-core double-single-accurate product, the double-single solve or the FP64 solve on "
+                         "--profile-columns columns of the matrix")
     ap.add_argument("--profile-columns", type=int, default=4096)
     ap.add_argument("--profile-n", type=int, default=0,
                     help="with --profile-kernel: a leading n x n block of the workload's matrix (0 = all of it)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for profilers: mixed inverse Lanczos on 4096 grid points, one untimed run")
+    ap.add_argument("--profile-recycle", action="store_true",
+                    help="small case for profilers: the recycling path (mixed, k = 16, r = 4) on the banded Toeplitz + "
+                         "noise matrix at n = 1200 on a 30 x 30 grid, one untimed run")
     ap.add_argument("--workload", default="triangular8000", choices=["triangular8000", "gaussian2000", "multi"],
                     help="multi: the multi-matrix workload through pseudo_grid_batch (one GPU, its own JSON line)")
     ap.add_argument("--matrices", type=int, default=16, help="with --workload multi: how many of the 64 matrices")
@@ -340,6 +356,19 @@ def main():
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.profile_recycle:
+        from paper_2606_26785_b300 import workloads as wl
+
+        T, _, _ = wl.schur(wl.toeplitz_noisy(1200, 5))
+        hr = p.Pseudo(T)
+        zr = torch.from_numpy(wl.grid(-1.5, 1.5, -1.0, 1.0, 30, 30)).cuda()
+        o = p.default_opts(mode=p.RECYCLE, precision=p.MIXED, rtol=1e-8, r=4, p_max=4, grid_nx=30, grid_ny=30,
+                           batch_b=20)
+        hr.grid(zr, (), opts=o)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_recycle": "toeplitz+noise n=1200, 30x30 grid, recycle mixed k=16",
+                          "stats": hr.stats()}))
+        return
     label, golden = WORKLOADS[args.workload]
     W, t_prep = make_workload(args.workload)
     fro = float(np.linalg.norm(W.T))
@@ -351,10 +380,12 @@ def main():
         X0 = torch.from_numpy(rng.standard_normal((nk, ncols)) + 1j * rng.standard_normal((nk, ncols))).cuda()
         zk = torch.from_numpy(W.z[:: max(1, W.z.size // ncols)][:ncols].copy()).cuda()
 
+        solve_prec = {"solve": p.MIXED, "solve_ds": p.DOUBLE_SINGLE, "solve_fp64": p.FP64}
+
         def call():
-            if args.profile_kernel == "solve":
+            if args.profile_kernel in solve_prec:
                 X = X0.clone()
-                h.solve(X, zk, adjoint=False, precision=p.MIXED)
+                h.solve(X, zk, adjoint=False, precision=solve_prec[args.profile_kernel])
             else:
                 h.matvec(X0, z=zk, precision=p.MIXED)
 
@@ -395,20 +426,21 @@ def main():
     flags = np.zeros(npts, np.int32)
     done = np.zeros(NB, bool)
 
-    def step(i, keep=True):
-        b = i % NB
-        out = h.grid(zb[b], eps, opts=opts, workspace=ws)
-        if keep:
-            torch.cuda.synchronize()
-            sigma[bidx[b]] = out["sigma"].cpu().numpy()
-            member[bidx[b]] = out["member"].cpu().numpy().astype(np.uint32)
-            flags[bidx[b]] = out["flags"].cpu().numpy()
-            done[b] = True
-        return bidx[b].size
+    def step(i):
+        return h.grid(zb[i % NB], eps, opts=opts, workspace=ws)
 
+    def keep(i, out):
+        b = i % NB
+        sigma[bidx[b]] = out["sigma"].cpu().numpy()
+        member[bidx[b]] = out["member"].cpu().numpy().astype(np.uint32)
+        flags[bidx[b]] = out["flags"].cpu().numpy()
+        done[b] = True
+
+    log(f"workload ready ({t_prep:.1f} s host prep); {NB} batches of about {npts // NB} points")
     for i in range(args.warmup):
-        step(i)
+        keep(i, step(i))
     torch.cuda.synchronize()
+    log("warm-up done")
     h.reset_stats()
     times, counted = [], 0
     clocks = Clocks(os.environ.get("PSEUDO_BENCH_CLOCKS_CSV", os.path.join(tempfile.gettempdir(), "bench_clocks.csv")))
@@ -422,13 +454,14 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            counted += step(i, keep=False)
+            out = step(i)
             e1.record()
             torch.cuda.synchronize()
             if dist:
                 dist.barrier()
             times.append(e0.elapsed_time(e1))
-            b = i % NB
+            counted += bidx[i % NB].size
+            keep(i, out)
     launches = p._abi.load().pseudo_launch_count() - lc0
     st = h.stats()
     ms = float(np.mean(times))
@@ -436,9 +469,10 @@ def main():
     pts_per_step = counted / max(1, args.steps)
     # outputs of every batch (the ones the timed steps did not keep are recomputed
     # untimed: the results are deterministic) for the accuracy checks
+    log(f"timed {args.steps} steps: {np.mean(times):.0f} ms per step")
     for b in range(NB):
         if not done[b]:
-            step(b)
+            keep(b, step(b))
     acc = {"oracle": check_accuracy(sigma, W, golden, rtol, member=member),
            "flags": {"converged": int(((flags & p._abi.PT_NOT_CONVERGED) == 0).sum()),
                      "not_converged": int(((flags & p._abi.PT_NOT_CONVERGED) != 0).sum()),
@@ -450,16 +484,18 @@ def main():
     # one profiled step: per-kernel CUDA-event times on the launching stream
     h.reset_stats()
     opts.profile = 1
-    step(0, keep=False)
+    step(0)
     torch.cuda.synchronize()
     opts.profile = 0
     kst = h.kernel_stats()
     prof_ms = h.stats()["ms_total"]
-    rf = roofline(kst, peaks, W.n, tensor_solve=opts.fp32_solver == 0)
+    solver = opts.fp32_solver if opts.fp32_solver != p._abi.SOLVER_AUTO else p.tuned_config(W.n)["fp32_solver"]
+    rf = roofline(kst, peaks, W.n, tensor_solve=solver == 0)
     if rf is not None:
         rf["share_of_step"] = max(kst.values(), key=lambda v: v["ms"])["ms"] / max(prof_ms, 1e-9)
 
     # end to end through the host-buffer C-ABI call (z in, results out, copies inside)
+    log("end-to-end steps")
     hopts = p.Opts.from_buffer_copy(opts)
     hopts.io_host = 1
     del ws
@@ -499,6 +535,7 @@ def main():
     if not args.no_extras and rank == 0:
         # plain FP64 inverse Lanczos on a sample of the grid: its speed (shift-batched and
         # per point) and the mixed result's error against it there
+        log("FP64 inverse Lanczos on a sample")
         stride = 97 if W.n >= 8000 else 20
         idx = np.arange(0, npts, stride)
         sub = torch.from_numpy(W.z[idx].copy()).cuda()
@@ -529,8 +566,18 @@ def main():
             acc["vs_fp64_every_point"]["fp64_seconds"] = time.perf_counter() - t0
         if args.workload == "triangular8000":
             h.close()
-            extras.update(gaussian_line(p, torch, eps))
-            extras.update(toeplitz_recycling(p, torch, eps))
+            t_ex = time.time()
+            for name, fn in (("gaussian2000_invlanc_mixed", lambda: gaussian_line(p, torch, eps)),
+                             ("multi_matrix_64", lambda: multi_line(64, 2, 1)),
+                             ("toeplitz_recycling", lambda: toeplitz_recycling(p, torch, eps))):
+                if time.time() - t_ex > args.extras_budget:
+                    extras[name] = {"skipped": f"comparison budget of {args.extras_budget:.0f} s spent"}
+                    continue
+                log(f"comparison {name}")
+                t1 = time.time()
+                extras[name] = fn()
+                extras[name]["wall_seconds"] = time.time() - t1
+        log("CPU baseline")
         cpu = cpu_baseline(W, args.workload)
 
     result = {
@@ -573,9 +620,8 @@ def gaussian_line(p, torch, eps):
     acc = check_accuracy(out["sigma"].cpu().numpy(), W, WORKLOADS["gaussian2000"][1], 1e-8,
                          member=out["member"].cpu().numpy())
     h.close()
-    return {"gaussian2000_invlanc_mixed": {"workload": WORKLOADS["gaussian2000"][0], "points": int(W.z.size),
-                                           "points_per_s": W.z.size / dt, "seconds": dt, "accuracy": acc,
-                                           "host_schur_seconds_untimed": t_schur}}
+    return {"workload": WORKLOADS["gaussian2000"][0], "points": int(W.z.size), "points_per_s": W.z.size / dt,
+            "seconds": dt, "accuracy": acc, "host_schur_seconds_untimed": t_schur}
 
 
 TOEPLITZ_N = 4000
@@ -595,6 +641,7 @@ def toeplitz_recycling(p, torch, eps):
     C = workloads.toeplitz_noisy(TOEPLITZ_N, 5)
     T, _, serr = workloads.schur(C)
     t_schur = time.time() - t0
+    log(f"toeplitz n={TOEPLITZ_N}: host Schur {t_schur:.1f} s")
     fro = float(np.linalg.norm(C))
     z = workloads.grid(-1.5, 1.5, -1.0, 1.0, TOEPLITZ_GRID, TOEPLITZ_GRID)
     zt = torch.from_numpy(z).cuda()
@@ -609,6 +656,7 @@ def toeplitz_recycling(p, torch, eps):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t1
         st = h.stats()
+        log(f"toeplitz {name}: {dt:.1f} s, accepted {int(st['n_accepted'])}")
         res[name] = {"points_per_s": z.size / dt, "seconds": dt, "accepted": int(st["n_accepted"]),
                      "refined": int(st["n_refined"]), "not_converged": int(st["n_not_converged"]),
                      "lobpcg_iters": int(st["lobpcg_iters"]), "sv_R": int(st["sv_R"])}
@@ -628,29 +676,28 @@ def toeplitz_recycling(p, torch, eps):
         rep["note"] = "against inverse Lanczos (mixed) at the points both report converged; band 2e-8"
         res[f"recycle_mixed_k{k}"]["vs_invlanc"] = rep
     h.close()
-    return {"toeplitz_recycling": {"workload": f"banded Toeplitz + noise n={TOEPLITZ_N} (seed 5), "
-                                               f"{TOEPLITZ_GRID}x{TOEPLITZ_GRID} grid over [-1.5,1.5]x[-1,1]",
-                                   "host_schur_seconds_untimed": t_schur, "schur_err": serr, **res}}
+    return {"workload": f"banded Toeplitz + noise n={TOEPLITZ_N} (seed 5), {TOEPLITZ_GRID}x{TOEPLITZ_GRID} grid "
+                        "over [-1.5,1.5]x[-1,1]", "host_schur_seconds_untimed": t_schur, "schur_err": serr, **res}
 
 
 BATCH_GOLDEN = ROOT / "tests" / "golden" / "batch16_samples.json"
 
 
-def run_multi(args):
+def multi_line(nm, steps, warmup):
     """The multi-matrix workload: independent complex Gaussian matrices
     N(0, 1/n), n log-uniform in [256, 2048] (seed 40), each on its own 64 x 64
-    grid over [-1.5, 1.5]^2; the first --matrices of its sequence (host Schur
-    factors not timed).  One step = one pseudo_grid_batch call over all of
-    them in mixed precision; the same matrices one after another with
-    pseudo_grid are timed beside it.  Accuracy: the stored oracle values of
-    the 8 smallest of the first 16 matrices."""
+    grid over [-1.5, 1.5]^2; the first nm of its sequence (host Schur factors
+    not timed).  One step = one pseudo_grid_batch call over all of them in
+    mixed precision (solver kernel and Lanczos slots from the tuned table); the
+    same matrices one after another with pseudo_grid are timed beside it.
+    Accuracy: the stored oracle values of the 8 smallest of the first 16
+    matrices."""
     import torch
 
     import paper_2606_26785_b300 as p
     from paper_2606_26785_b300 import workloads
     from tests.parity import check_sigma
 
-    nm = args.matrices
     t0 = time.time()
     mats = workloads.gaussian_batch(64, 40)[:nm]
     Ts, errs = [], []
@@ -664,7 +711,7 @@ def run_multi(args):
     z = torch.from_numpy(zh).cuda()
     hs = [p.Pseudo(T) for T in Ts]
     opts = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
-    eps = (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9, 1e-10)
+    eps = workloads.EPS_LEVELS
     npts = nm * zh.size
 
     def timed(fn):
@@ -676,15 +723,15 @@ def run_multi(args):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), r
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         outs, _ = p.grid_batch(hs, [z] * nm, eps, opts=opts)
     lc0 = p._abi.load().pseudo_launch_count()
-    t_batch = [timed(lambda: p.grid_batch(hs, [z] * nm, eps, opts=opts)) for _ in range(args.steps)]
-    launches = (p._abi.load().pseudo_launch_count() - lc0) // max(1, args.steps)
+    t_batch = [timed(lambda: p.grid_batch(hs, [z] * nm, eps, opts=opts)) for _ in range(steps)]
+    launches = (p._abi.load().pseudo_launch_count() - lc0) // max(1, steps)
     outs = t_batch[-1][1][0]
     ms = float(np.mean([t for t, _ in t_batch]))
     ms_seq = float(np.mean([timed(lambda: [h.grid(z, eps, opts=opts) for h in hs])[0]
-                            for _ in range(max(1, min(2, args.steps)))]))
+                            for _ in range(max(1, min(2, steps)))]))
     acc = None
     if BATCH_GOLDEN.exists():
         g = json.loads(BATCH_GOLDEN.read_text())
@@ -700,15 +747,27 @@ def run_multi(args):
                 bad += rep["n_bad"]
                 worst = max(worst, abs(v - s_["sigma_ref"]) / s_["sigma_ref"])
             acc = {"n_points": len(smp), "n_bad": int(bad), "max_rel_err": worst}
+    for h in hs:
+        h.close()
+    return {"value": npts / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "gpu_launches": int(launches),
+            "workload": f"multi-matrix: first {nm} of 64 complex Gaussian matrices N(0,1/n), n log-uniform in "
+                        "[256,2048] (seed 40), 64x64 grid each over [-1.5,1.5]^2",
+            "sizes": sizes, "points": npts, "host_schur_s": t_prep,
+            "sequential_pseudo_grid": {"ms": ms_seq, "points_per_s": npts / (ms_seq / 1e3)},
+            "speedup_over_sequential": ms_seq / ms, "accuracy": acc}
+
+
+def run_multi(args):
+    """--workload multi: the multi-matrix workload (multi_line) as its own JSON line."""
+    r = multi_line(args.matrices, args.steps, args.warmup)
     print(json.dumps({
-        "metric": METRIC, "value": npts / (ms / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64+f32",
-        "data": "synthetic", "gpu_launches": int(launches),
-        "config": {"workload": f"multi-matrix: first {nm} of 64 complex Gaussian matrices N(0,1/n), "
-                               "n log-uniform in [256,2048] (seed 40), 64x64 grid each over [-1.5,1.5]^2",
-                   "sizes": sizes, "points": npts, "host_schur_s": t_prep},
-        "sequential_pseudo_grid": {"ms": ms_seq, "points_per_s": npts / (ms_seq / 1e3)},
-        "accuracy": acc}))
+        "metric": METRIC, "value": r["value"], "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "dtype": "f64+f32",
+        "data": "synthetic", "gpu_launches": r["gpu_launches"],
+        "config": {"workload": r["workload"], "sizes": r["sizes"], "points": r["points"],
+                   "host_schur_s": r["host_schur_s"]},
+        "sequential_pseudo_grid": r["sequential_pseudo_grid"], "accuracy": r["accuracy"]}))
 
 
 def run_reference(args, rank, world):

@@ -62,6 +62,8 @@ enum { PSEUDO_FP64 = 0, PSEUDO_MIXED = 1 };
 enum { PSEUDO_MIXED_CUDACORE = 2 };
 /* pseudo_solve only: the solve in double-single arithmetic on the FP32 units */
 enum { PSEUDO_DOUBLE_SINGLE = 3 };
+/* pseudo_opts.fp32_solver: chosen per matrix order from the tuned table */
+enum { PSEUDO_SOLVER_AUTO = 2 };
 
 /* grid traversal of the recycling path (pseudo_opts.traversal):
  * BATCH_ZIGZAG = the batch-zigzag order of Sec. 2.3 with column batches of
@@ -111,7 +113,9 @@ typedef struct {
     int profile;        /* 1: time every hot-kernel launch with CUDA events (pseudo_kernel_stats) */
     int fp32_solver;    /* mixed precision: the FP32 triangular solves run on 0 = the tensor
                            cores (tcgen05, operands split hi + lo into TF32, 3 products),
-                           1 = the CUDA cores (FP32 FMA) */
+                           1 = the CUDA cores (FP32 FMA), PSEUDO_SOLVER_AUTO (default) = the
+                           choice of the library's tuned table for the matrix order
+                           (pseudo_tuned_config) */
     int traversal;      /* RECYCLE on a Cartesian grid: the visiting order, PSEUDO_TRAVERSE_* */
 } pseudo_opts;
 
@@ -244,6 +248,15 @@ int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t n
  * Host-only: needs no handle and no device.  Errors: ARG. */
 int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int traversal,
                            int32_t *order);
+
+/* The library's tuned choices for a matrix of order n (the benchmark spec batching
+ * pattern's autotuner; the paper has no counterpart): the FP32 solver kernel
+ * that pseudo_opts.fp32_solver = PSEUDO_SOLVER_AUTO selects (0 tensor cores,
+ * 1 CUDA cores) and the number of Lanczos slots (shifts per solve launch)
+ * that shift_batch = 0 selects in inverse-Lanczos mode.  The table comes from
+ * an offline sweep on this part, per bucket of n.  Either pointer may be NULL.
+ * Host-only.  Errors: ARG (n < 1). */
+int pseudo_tuned_config(int64_t n, int *fp32_solver, int *slots);
 
 /* Counters and phase timings accumulated since create or the last reset. */
 int pseudo_stats(pseudo_handle h, pseudo_stats_t *out);

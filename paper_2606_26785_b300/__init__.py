@@ -15,7 +15,7 @@ from ._abi import (  # noqa: F401
     DOUBLE_SINGLE, FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON, Opts,
     PseudoError, Stats, check)
 
-__all__ = ["Pseudo", "grid_batch", "traversal_order", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE",
+__all__ = ["Pseudo", "grid_batch", "traversal_order", "tuned_config", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE",
            "DOUBLE_SINGLE", "INVLANC",
            "RECYCLE", "TRAVERSE_BATCH_ZIGZAG", "TRAVERSE_HILBERT", "TRAVERSE_MORTON", "PseudoError"]
 
@@ -251,6 +251,15 @@ def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=N
         ctypes.byref(o), ptrs("sigma"), ptrs("res"), ptrs("flags"), ptrs("member"), _ptr(workspace),
         workspace.numel(), _stream_ptr(stream)))
     return outs, rc
+
+
+def tuned_config(n: int) -> dict:
+    """The library's tuned choices for order n (pseudo_tuned_config): the FP32
+    solver kernel of fp32_solver = SOLVER_AUTO and the Lanczos slots of
+    shift_batch = 0."""
+    s, k = ctypes.c_int(), ctypes.c_int()
+    check(_abi.load().pseudo_tuned_config(int(n), ctypes.byref(s), ctypes.byref(k)))
+    return {"fp32_solver": s.value, "slots": k.value}
 
 
 def traversal_order(grid_nx: int, grid_ny: int, batch_b: int = 20, traversal: int = TRAVERSE_BATCH_ZIGZAG,

@@ -12,6 +12,7 @@ ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT = 
 INVLANC, RECYCLE = 0, 1
 FP64, MIXED, MIXED_CUDACORE, DOUBLE_SINGLE = 0, 1, 2, 3
 TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON = 0, 1, 2
+SOLVER_TENSOR_CORES, SOLVER_CUDA_CORES, SOLVER_AUTO = 0, 1, 2
 PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4, 8, 16
 
 EXPORTED = (
@@ -19,7 +20,7 @@ EXPORTED = (
     "pseudo_stats_reset", "pseudo_info", "pseudo_destroy", "pseudo_last_error", "pseudo_solve_workspace_bytes",
     "pseudo_solve", "pseudo_matvec", "pseudo_kernel_stats", "pseudo_launch_count", "pseudo_recycle_state_layout",
     "pseudo_grid_batch_workspace_bytes", "pseudo_grid_batch", "pseudo_matvec_workspace_bytes",
-    "pseudo_traversal_order", "pseudo_set_wait_limit", "pseudo_solve_noalloc",
+    "pseudo_traversal_order", "pseudo_set_wait_limit", "pseudo_solve_noalloc", "pseudo_tuned_config",
 )
 
 
@@ -95,6 +96,7 @@ def load(build_if_missing: bool = True):
     lib.pseudo_grid_batch_workspace_bytes.argtypes = [vp, ci, vp, po, ctypes.POINTER(ctypes.c_size_t)]
     lib.pseudo_grid_batch.argtypes = [vp, ci, vp, vp, vp, ci, po, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
     lib.pseudo_set_wait_limit.argtypes = [vp, ctypes.c_uint64]
+    lib.pseudo_tuned_config.argtypes = [i64, ctypes.POINTER(ci), ctypes.POINTER(ci)]
     lib.pseudo_solve_noalloc.argtypes = [vp, vp, vp, i64, ci, vp]
     for name in EXPORTED:
         fn = getattr(lib, name)

@@ -12,6 +12,9 @@ constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
 int set_err(int code, const char *fmt, ...);
 int cuda_err(cudaError_t e, const char *where);
 void clear_err();
+// the tuned table of autotune_table.h: FP32 solver kernel and Lanczos slots for order n
+int tuned_fp32_solver(int n);
+int tuned_slots(int n);
 
 // Bump allocator over the caller's workspace (256-byte aligned pieces).  With
 // a null base it only measures.

@@ -22,6 +22,7 @@
 #include <cmath>
 #include <vector>
 
+#include "autotune_table.h"
 #include "common.cuh"
 #include "driver.h"
 #include "internal.h"
@@ -69,8 +70,19 @@ constexpr int FB_SLOTS = 1024;
 // would contract by less than 4 per step
 constexpr double FB_KU = 1.0 / 32.0;
 
+int tuned_fp32_solver(int n) {
+    for (const TunePoint &t : kTuneTable)
+        if (n <= t.n_max) return t.fp32_solver;
+    return kTuneTable[sizeof(kTuneTable) / sizeof(kTuneTable[0]) - 1].fp32_solver;
+}
+int tuned_slots(int n) {
+    for (const TunePoint &t : kTuneTable)
+        if (n <= t.n_max) return t.slots;
+    return kTuneTable[sizeof(kTuneTable) / sizeof(kTuneTable[0]) - 1].slots;
+}
+
 static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool fp32, int mmax) {
-    int64_t S = o->shift_batch > 0 ? o->shift_batch : 8192;
+    int64_t S = o->shift_batch > 0 ? o->shift_batch : tuned_slots(h->n);
     S = std::min<int64_t>(S, npts);
     const double esz = fp32 ? 8.0 : 16.0;
     while (S > 32) {

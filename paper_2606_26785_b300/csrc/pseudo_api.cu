@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/pseudo.h: handle set-up (packed
 // panels of T, norms), argument checking, workspace carving, and the grid
 // drivers (inverse Lanczos here; recycling in recycle_driver.cu).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -72,6 +73,7 @@ int pseudo_opts_default(pseudo_opts *o) {
     o->maxiter_lobpcg = 60;
     o->max_ir = 6;
     o->seed = 12345;
+    o->fp32_solver = PSEUDO_SOLVER_AUTO;
     return PSEUDO_OK;
 }
 
@@ -173,6 +175,14 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(e, "create"));
     memset(&h->stats, 0, sizeof h->stats);
     *out = h;
+    return PSEUDO_OK;
+}
+
+int pseudo_tuned_config(int64_t n, int *fp32_solver, int *slots) {
+    clear_err();
+    if (n < 1) return set_err(PSEUDO_ERR_ARG, "n must be >= 1");
+    if (fp32_solver) *fp32_solver = tuned_fp32_solver((int)std::min<int64_t>(n, 1 << 30));
+    if (slots) *slots = tuned_slots((int)std::min<int64_t>(n, 1 << 30));
     return PSEUDO_OK;
 }
 
@@ -340,6 +350,7 @@ static int check_opts(const pseudo_opts *o) {
         return set_err(PSEUDO_ERR_ARG, "maxiter_lanczos must be in [1, %d]", LANCZOS_MMAX);
     if (o->max_ir < 1 || o->max_ir > 32) return set_err(PSEUDO_ERR_ARG, "max_ir must be in [1, 32]");
     if (o->shift_batch < 0) return set_err(PSEUDO_ERR_ARG, "shift_batch < 0");
+    if (o->fp32_solver < 0 || o->fp32_solver > PSEUDO_SOLVER_AUTO) return set_err(PSEUDO_ERR_ARG, "bad fp32_solver");
     if (!(o->rtol >= 0.0)) return set_err(PSEUDO_ERR_ARG, "rtol < 0");
     if (o->mode == PSEUDO_RECYCLE) {
         if (o->r < 1 || o->r > 8) return set_err(PSEUDO_ERR_ARG, "r must be in [1, 8]");
@@ -391,7 +402,13 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     if (o->io_host) {
         for (int64_t i = 0; i < npts; ++i)
             if (!std::isfinite(z[i].re) || !std::isfinite(z[i].im)) return set_err(PSEUDO_ERR_NONFINITE, "z[%lld] is not finite", (long long)i);
-    } else {
+    }
+    size_t need = 0;
+    pseudo_workspace_bytes(h, o, npts, &need);
+    if (!workspace || workspace_bytes < need)
+        return set_err(PSEUDO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, need);
+    if (((uintptr_t)workspace) & 255) return set_err(PSEUDO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    if (!o->io_host) {
         // device shifts: one pass over z before any other work
         cudaStream_t s0 = (cudaStream_t)stream;
         int zbad = 0;
@@ -402,11 +419,6 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
         if (ez != cudaSuccess) return cuda_err(ez, "checking z");
         if (zbad) return set_err(PSEUDO_ERR_NONFINITE, "z has non-finite entries");
     }
-    size_t need = 0;
-    pseudo_workspace_bytes(h, o, npts, &need);
-    if (!workspace || workspace_bytes < need)
-        return set_err(PSEUDO_ERR_WORKSPACE, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes, need);
-    if (((uintptr_t)workspace) & 255) return set_err(PSEUDO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     GridIO io;
     io.z = (const double2 *)z;
     io.npts = npts;
@@ -422,7 +434,7 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     h->prof = o->profile != 0;
     h->recs.clear();
     h->evn = 0;
-    h->fp32_solver = o->fp32_solver;
+    h->fp32_solver = o->fp32_solver == PSEUDO_SOLVER_AUTO ? tuned_fp32_solver(h->n) : o->fp32_solver;
     int res = o->mode == PSEUDO_INVLANC ? invlanc_run(h, o, io, c, s) : recycle_run(h, o, io, c, s);
     if (res >= 0 && o->precision == PSEUDO_MIXED) {
         const int rc = check_dev_err(h, s);

@@ -110,20 +110,37 @@ def test_non_finite_inputs():
 
 @pytest.mark.parametrize("mode", [0, 1])
 def test_workspace_one_byte_short(mode):
+    """Through the C ABI directly (the Python binding would allocate a big
+    enough workspace itself): one byte short is refused before any launch,
+    the exact size works."""
+    import ctypes
+
     import torch
 
     import paper_2606_26785_b300 as p
 
+    lib = p._abi.load()
     W = workloads.make("grcar", nx=6, ny=5, n=60)
     h = p.Pseudo(W.T)
     o = p.default_opts(mode=mode, precision=p.MIXED, rtol=1e-8, r=4, p_max=4, grid_nx=W.nx, grid_ny=W.ny, batch_b=5)
     need = h.workspace_bytes(W.z.size, o)
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    with pytest.raises(p.PseudoError) as ei:
-        h.grid(W.z, (), opts=o, workspace=ws[: need - 1])
-    assert ei.value.code == p._abi.ERR_WORKSPACE
-    out = h.grid(W.z, (), opts=o, workspace=ws)
-    assert out["status"] >= 0
+    z = torch.from_numpy(W.z).cuda()
+    sig = torch.empty(W.z.size, dtype=torch.float64, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    vp = ctypes.c_void_p
+
+    def call(nbytes):
+        return lib.pseudo_grid(h._h, vp(z.data_ptr()), W.z.size, None, 0, ctypes.byref(o), vp(sig.data_ptr()), None,
+                               None, None, vp(ws.data_ptr()), nbytes, stream)
+
+    before = lib.pseudo_launch_count()
+    assert call(need - 1) == p._abi.ERR_WORKSPACE
+    assert lib.pseudo_launch_count() == before
+    assert b"workspace" in lib.pseudo_last_error()
+    assert call(need) >= 0
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(sig.cpu().numpy()))
     h.close()
 
 
