@@ -171,12 +171,19 @@ def compare_with_fp64(sig, s64, fro, n, rtol=1e-8, member=None, member64=None, e
     return rep
 
 
+# Arithmetic rates of this machine's B300 measured by paper_2606_26785_b300/probe/peaks.cu
+# (python -m paper_2606_26785_b300.probe.peaks): FP64 FMA 1.010, FP64 tensor-core MMA
+# (m8n8k4) 1.053 and FP32 FMA 73.48 TFLOP/s.  The FP64 roofline is the larger FP64 rate.
+FP64_MEASURED_TFLOPS = 1.053
+FP32_MEASURED_TFLOPS = 73.48
+# double-single on the FP32 units: 44 FP32 instructions per complex multiply-add
+# (8 algorithmic flops) in the solve, 12 per real multiply-add (2 flops) in the product
+DS_SOLVE_TFLOPS = FP32_MEASURED_TFLOPS / 2.0 * 8.0 / 44.0
+
+
 def _nominal_fp32_tflops(peaks):
-    """FP32 FMA pipe: 148 SMs x 128 lanes x 2 flops x max SM clock."""
-    return 148 * 128 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-
-
-FP64_MEASURED_TFLOPS = 1.13  # B300 FP64 FMA rate measured with independent DFMA chains on all SMs
+    """FP32 FMA pipe as measured (probe above)."""
+    return FP32_MEASURED_TFLOPS
 
 
 def _tf32x3_tflops(peaks):
@@ -236,6 +243,8 @@ def roofline(kst, peaks, n, tensor_solve=True):
     elif name == "trmv_ds":
         # double-single: 12 FP32 operations per real multiply-add (2 algorithmic flops)
         peak, unit, bound = fp32 / 6.0, "TFLOP/s", "alu"
+    elif name == "trsv_ds":
+        peak, unit, bound = DS_SOLVE_TFLOPS, "TFLOP/s", "alu"
     elif name == "lanczos":
         achieved = k["bytes"] / k["launches"] / (per_launch_ms / 1e3) / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -247,8 +256,11 @@ def roofline(kst, peaks, n, tensor_solve=True):
     return {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": None, "launches": k["launches"], "avg_launch_ms": per_launch_ms,
             "algorithmic_flops_per_launch": flops, "share_of_step": None,
-            "peak_source": "derived from 148 SMs x 128 FP32 lanes x max clock" if name in ("trsv32", "trmv_ds")
-            else "measured FP64 DFMA probe"}
+            "peak_source": {"trsv32": "measured FP32 FMA rate (probe)",
+                            "trmv_ds": "measured FP32 FMA rate / 6 (12 FP32 instructions per real multiply-add)",
+                            "trsv_ds": "measured FP32 FMA rate / 2 x 8 / 44 (FP32 instructions per complex "
+                                       "multiply-add of the double-single solve)"}.get(
+                name, "measured FP64 rate (tensor-core MMA, probe)")}
 
 
 def oracle_sample(W, workload, threads):

@@ -88,6 +88,27 @@ def test_argument_errors_are_reported_before_any_device_work():
     assert lib.pseudo_matvec(None, buf, None, buf, buf, c64(1), 0, 0, 0, buf, ctypes.c_size_t(64),
                              None) == _abi.ERR_ARG
     assert lib.pseudo_stats(None, None) == _abi.ERR_ARG
+    assert lib.pseudo_set_wait_limit(None, ctypes.c_uint64(0)) == _abi.ERR_ARG
+    assert lib.pseudo_solve_noalloc(None, buf, buf, c64(1), 0, None) == _abi.ERR_ARG
+    assert lib.pseudo_tuned_config(c64(0), None, None) == _abi.ERR_ARG
+
+
+def test_tuned_table_covers_every_order():
+    """The tuned table (pseudo_tuned_config, host-only) gives a valid solver
+    kernel and a positive slot count for every order, piecewise constant over
+    buckets, and the default options ask for it."""
+    import paper_2606_26785_b300 as p
+    from paper_2606_26785_b300 import _abi
+
+    assert p.default_opts().fp32_solver == _abi.SOLVER_AUTO
+    prev = None
+    changes = 0
+    for n in list(range(1, 4100, 7)) + [8000, 16000, 1 << 20]:
+        c = p.tuned_config(n)
+        assert c["fp32_solver"] in (0, 1) and c["slots"] >= 1
+        changes += prev is not None and c != prev
+        prev = c
+    assert changes <= 16
 
 
 def test_last_error_is_per_thread():
