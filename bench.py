@@ -636,27 +636,32 @@ def gaussian_line(p, torch, eps):
             "seconds": dt, "accuracy": acc, "host_schur_seconds_untimed": t_schur}
 
 
-TOEPLITZ_N = 4000
-TOEPLITZ_GRID = 100
+TOEPLITZ_GOLDEN = ROOT / "tests" / "golden" / "toeplitz1200_samples.json"
 
 
 def toeplitz_recycling(p, torch, eps):
     """The recycled Rayleigh--Ritz-SVD path (Alg. 3) next to inverse Lanczos on
     the banded Toeplitz + noise matrix (superdiagonal 1, subdiagonal 0.25,
-    complex Gaussian noise 1e-3/sqrt(n), seed 5) at n = TOEPLITZ_N on a
-    TOEPLITZ_GRID^2 grid over the workload's window [-1.5, 1.5] x [-1, 1], in
-    mixed precision at recycled ranks k = 8, 32, 64 (r = 4): acceptance counts,
-    points/s and the agreement of every result with inverse Lanczos."""
+    complex Gaussian noise 1e-3/sqrt(n), seed 5) at n = 1200 on a 50 x 50 grid
+    over the workload's window [-1.5, 1.5] x [-1, 1], in mixed precision at
+    recycled ranks k = 8, 32, 64 (r = 4): acceptance counts, points/s, the
+    agreement of every converged result with inverse Lanczos, and the stored
+    oracle values (tests/golden/toeplitz1200_samples.json) at the points
+    reported converged."""
     from paper_2606_26785_b300 import workloads
+    from tests.parity import check_sigma
 
+    g = json.loads(TOEPLITZ_GOLDEN.read_text())
+    n, nx, ny = g["n"], g["nx"], g["ny"]
     t0 = time.time()
-    C = workloads.toeplitz_noisy(TOEPLITZ_N, 5)
+    C = workloads.toeplitz_noisy(n, 5)
     T, _, serr = workloads.schur(C)
     t_schur = time.time() - t0
-    log(f"toeplitz n={TOEPLITZ_N}: host Schur {t_schur:.1f} s")
+    log(f"toeplitz n={n}: host Schur {t_schur:.1f} s")
     fro = float(np.linalg.norm(C))
-    z = workloads.grid(-1.5, 1.5, -1.0, 1.0, TOEPLITZ_GRID, TOEPLITZ_GRID)
+    z = workloads.grid(-1.5, 1.5, -1.0, 1.0, nx, ny)
     zt = torch.from_numpy(z).cuda()
+    idx = np.array(g["index"])
     h = p.Pseudo(T)
     res = {}
 
@@ -669,27 +674,31 @@ def toeplitz_recycling(p, torch, eps):
         dt = time.perf_counter() - t1
         st = h.stats()
         log(f"toeplitz {name}: {dt:.1f} s, accepted {int(st['n_accepted'])}")
+        sig, fl = out["sigma"].cpu().numpy(), out["flags"].cpu().numpy()
+        conv = (fl[idx] & p._abi.PT_NOT_CONVERGED) == 0
+        orep = check_sigma(sig[idx][conv], np.array(g["sigma_ref"])[conv], n=n, fro=g["fro_norm"], schur_err=serr,
+                           oracle_off=np.array(g["oracle_off"])[conv], rtol=1e-8)
+        orep["not_converged_of_stored"] = int((~conv).sum())
         res[name] = {"points_per_s": z.size / dt, "seconds": dt, "accepted": int(st["n_accepted"]),
                      "refined": int(st["n_refined"]), "not_converged": int(st["n_not_converged"]),
-                     "lobpcg_iters": int(st["lobpcg_iters"]), "sv_R": int(st["sv_R"])}
-        return out
+                     "lobpcg_iters": int(st["lobpcg_iters"]), "sv_R": int(st["sv_R"]),
+                     "rtilde_capped": int(st["n_rtilde_capped"]), "oracle": orep}
+        return sig, fl
 
     o_inv = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
     h.grid(zt[:64], eps, opts=o_inv)
-    ref = run("invlanc_mixed", o_inv)
-    s_ref, f_ref = ref["sigma"].cpu().numpy(), ref["flags"].cpu().numpy()
+    s_ref, f_ref = run("invlanc_mixed", o_inv)
     for k in (8, 32, 64):
-        o = p.default_opts(mode=p.RECYCLE, precision=p.MIXED, rtol=1e-8, r=4, p_max=k // 4, grid_nx=TOEPLITZ_GRID,
-                           grid_ny=TOEPLITZ_GRID, batch_b=20)
-        out = run(f"recycle_mixed_k{k}", o)
-        sig, fl = out["sigma"].cpu().numpy(), out["flags"].cpu().numpy()
+        o = p.default_opts(mode=p.RECYCLE, precision=p.MIXED, rtol=1e-8, r=4, p_max=k // 4, grid_nx=nx, grid_ny=ny,
+                           batch_b=20)
+        sig, fl = run(f"recycle_mixed_k{k}", o)
         both = ((fl | f_ref) & p._abi.PT_NOT_CONVERGED) == 0
-        rep = compare_with_fp64(sig[both], s_ref[both], fro, TOEPLITZ_N, 2e-8)
+        rep = compare_with_fp64(sig[both], s_ref[both], fro, n, 2e-8)
         rep["note"] = "against inverse Lanczos (mixed) at the points both report converged; band 2e-8"
         res[f"recycle_mixed_k{k}"]["vs_invlanc"] = rep
     h.close()
-    return {"workload": f"banded Toeplitz + noise n={TOEPLITZ_N} (seed 5), {TOEPLITZ_GRID}x{TOEPLITZ_GRID} grid "
-                        "over [-1.5,1.5]x[-1,1]", "host_schur_seconds_untimed": t_schur, "schur_err": serr, **res}
+    return {"workload": f"banded Toeplitz + noise n={n} (seed 5), {nx}x{ny} grid over [-1.5,1.5]x[-1,1]",
+            "host_schur_seconds_untimed": t_schur, "schur_err": serr, **res}
 
 
 BATCH_GOLDEN = ROOT / "tests" / "golden" / "batch16_samples.json"

@@ -215,8 +215,12 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
         launch_normalize(L.X64, n, F, L.mask, s);
         cudaMemcpyAsync(L.Ufin, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
-    // Rayleigh quotient and residual of the returned vectors
-    const bool hp = L.fp32 || L.ds;
+    // Rayleigh quotient and residual of the returned vectors: double-single-
+    // accurate products on the tensor cores for the FP32 pass; FP64 products
+    // for the double-single pass, whose points are the ill-conditioned ones
+    // with strongly graded singular vectors, where an error relative to the
+    // row and column maxima would swamp sigma
+    const bool hp = L.fp32;
     const int kc = hp ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
     int k0 = kp_begin(h, s);
     trmv_hp(h, hp, 0, nullptr, L.fin_z, P, L.Ufin, F, nullptr, F, L.Y, F, 0, s, L.xh, L.xl, L.oz);
@@ -225,7 +229,8 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     h->stats.mv_M_fp64_refine += 2 * (int64_t)P;
     launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);
     // kappa * u above 1/32: the planned refinement contracts by less than 4 per step
-    launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, hp ? 1 : 0, h->norm2, L.eps,
+    launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, (L.fp32 || L.ds) ? 1 : 0,
+                       h->norm2, L.eps,
                        neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), FB_KU,
                        L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;

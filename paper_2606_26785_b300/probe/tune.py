@@ -72,7 +72,12 @@ def table_text(rows, orders, gpu):
     # bucket edges halfway (geometrically) between the swept orders; orders above
     # the last swept one keep the untuned defaults (tensor cores, 8192 slots)
     edges = [int(round((a * b) ** 0.5)) for a, b in zip(orders[:-1], orders[1:])] + [int(round(orders[-1] * 1.41))]
-    lines = [f"    {{{e}, {best[n]['fp32_solver']}, {best[n]['slots']}}},"
+    # a slot count at or above the sweep's 4,096 points cannot be told from a
+    # larger one there: such entries get the largest count
+    def slots(r):
+        return max(SLOTS) if r["slots"] >= 4096 else r["slots"]
+
+    lines = [f"    {{{e}, {best[n]['fp32_solver']}, {slots(best[n])}}},"
              f"  // n = {n}: {best[n]['points_per_s']:.0f} points/s" for n, e in zip(orders, edges)]
     lines.append("    {1 << 30, 0, 8192},  // larger orders: not swept (the defaults)")
     stamp = datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%d")

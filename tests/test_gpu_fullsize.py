@@ -62,6 +62,37 @@ def test_triangular8000_mixed_matches_fp64():
     h.close()
 
 
+def test_triangular8000_stored_oracle_points():
+    """The strongly nonnormal triangular workload (n = 8000, seed 3, 300 x 300
+    grid) in the launch configuration bench.py times (strided batches of every
+    20th grid point, mixed precision, rtol 1e-8) against the stored oracle
+    values at the grid's rim (tests/golden/triangular8000_samples.json, written
+    by tests/golden/make_triangular_samples.py), under the pass rule including
+    the relative-only test above 1e-6 ||T||_F, with identical membership."""
+    import paper_2606_26785_b300 as p
+
+    g = json.loads((GOLD / "triangular8000_samples.json").read_text())
+    T = workloads.triangular(g["n"], 3)
+    z = workloads.grid(-1.5, 1.5, -1.5, 1.5, g["nx"], g["ny"])
+    h = p.Pseudo(T)
+    got, mem = {}, {}
+    for b in sorted({i % 20 for i in g["index"]}):
+        idx = np.arange(b, z.size, 20)
+        out = h.grid(z[idx], workloads.EPS_LEVELS, mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
+        sig, m = out["sigma"].cpu().numpy(), out["member"].cpu().numpy()
+        for j, i in enumerate(idx):
+            got[int(i)], mem[int(i)] = sig[j], m[j]
+    sig = np.array([got[i] for i in g["index"]])
+    member = np.array([mem[i] for i in g["index"]])
+    rep = check_sigma(sig, np.array(g["sigma_ref"]), n=g["n"], fro=g["fro_norm"], schur_err=0.0,
+                      oracle_off=np.array(g["oracle_off"]), rtol=1e-8, eps_levels=workloads.EPS_LEVELS,
+                      member=member)
+    print(rep)
+    assert rep["n_bad"] == 0 and rep["member_mismatch"] == 0, rep
+    assert rep["n_rel_only"] == len(g["index"]), rep
+    h.close()
+
+
 @pytest.mark.parametrize("mode,k", [("recycle", 8), ("recycle", 32), ("recycle", 64), ("invlanc", 0)])
 def test_toeplitz1200_mixed(mode, k):
     """The banded Toeplitz + noise workload, reduced to n = 1200 on a 50 x 50

@@ -75,9 +75,9 @@ def test_solve_fp32_tensor_cores(n, ncols, adjoint):
 def test_solve_double_single(n, ncols, adjoint):
     """The double-single solve (FP32 pairs on the CUDA cores, the solve of the
     points the FP32 solves cannot serve) against the oracle's substitution:
-    about 2^-46 relative per operation, so within 1e-12 on these
-    well-conditioned shifts, across ragged 64-row panels and both the narrow
-    (up to 296 columns) and the 8-column groups."""
+    about 2^-46 relative per operation, so within 1e-11 on these
+    well-conditioned shifts (FP32 solves: 1e-4), across ragged 64-row panels
+    and both the narrow (up to 296 columns) and the 8-column groups."""
     import torch
 
     import paper_2606_26785_b300 as p
@@ -90,7 +90,7 @@ def test_solve_double_single(n, ncols, adjoint):
     got = X.cpu().numpy()
     rel = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
     h.close()
-    assert rel.max() < 1e-12, rel.max()
+    assert rel.max() < 1e-11, rel.max()
 
 
 @pytest.mark.parametrize("n", [1, 3, 65, 130])
