@@ -78,7 +78,8 @@ enum {
     PSEUDO_PT_REFINED = 2,       /* refined by LOBPCG-SVD / Lanczos */
     PSEUDO_PT_NOT_CONVERGED = 4, /* iteration cap hit; best estimate returned */
     PSEUDO_PT_IR_FALLBACK = 8,   /* mixed precision: kappa too large for the FP32 solves; the
-                                    point was redone with double-single (about 2^-46) solves */
+                                    point was redone in FP64 (or found singular to working
+                                    precision, PSEUDO_PT_SINGULAR) */
     PSEUDO_PT_SINGULAR = 16      /* sigma_min(T - zI) is below FP64 working precision (z on a
                                     diagonal entry of T, or deep inside the pseudospectrum of a
                                     strongly nonnormal T): sigma_out is an upper bound at the
@@ -130,8 +131,7 @@ typedef struct {
     int64_t n_updates;   /* updateRecy calls */
     int64_t lanczos_steps;
     int64_t lobpcg_iters;
-    int64_t n_fallback;  /* mixed precision: points redone with double-single solves
-                            (PSEUDO_PT_IR_FALLBACK) */
+    int64_t n_fallback;  /* mixed precision: points handed to the FP64 pass (PSEUDO_PT_IR_FALLBACK) */
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
     int64_t n_singular;  /* of those, points found singular to working precision (PSEUDO_PT_SINGULAR) */
     int64_t n_rtilde_capped; /* recycle mode: recySing evaluations whose r~ of eq. (tau) exceeded the

@@ -15,9 +15,8 @@
 // result (computed in double-single).  Mixed-precision points whose condition
 // kappa = (||T||_2 + |z|) / sigma is too large for the FP32 solves are handed
 // to a second pass: first a one-step test for sigma below working precision
-// (fallback_triage), then inverse Lanczos with FP64 vectors and double-single
-// solves (about 2^-46 relative, six times the FP64 rate on this part), sigma
-// again the Rayleigh quotient of the Ritz vector.
+// (fallback_triage, double-single solves), then FP64 inverse Lanczos for the
+// points it does not settle.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -32,9 +31,6 @@ namespace pseudo {
 struct LancLayout {
     int S = 0, F = 0, mmax = 0;
     bool fp32 = false;
-    // FP64 vectors with double-single solves (the pass that takes the points
-    // FP32 cannot serve); sigma is then the Rayleigh quotient of the Ritz vector
-    bool ds = false;
     void *Q = nullptr, *W = nullptr, *xs = nullptr;
     double *alpha = nullptr, *beta = nullptr, *svec = nullptr, *theta = nullptr;
     double2 *Hp = nullptr;                           // Gram-Schmidt coefficients, S x (mmax+1)
@@ -54,7 +50,7 @@ struct LancLayout {
     double *sig_dev = nullptr, *res_dev = nullptr;
     int32_t *flags_dev = nullptr;
     uint32_t *member_dev = nullptr;
-    // mixed precision: points redone in the double-single pass (list, count) and the compact
+    // mixed precision: points redone in the FP64 pass (list, count) and the compact
     // per-chunk arrays of that pass (capacity CH)
     int *fb_list = nullptr, *fb_cnt = nullptr;
     int CH = 0;
@@ -64,9 +60,10 @@ struct LancLayout {
     uint32_t *fb_member = nullptr;
 };
 
-// Slots of the double-single pass that mixed precision hands its hard points to.
-constexpr int FB_SLOTS = 1024;
-// kappa * u above which a point goes to the double-single pass: the planned refinement
+// Slots of the FP64 pass that mixed precision hands its hard points to (few
+// columns per launch: the FP64 solve spreads them over narrow column groups).
+constexpr int FB_SLOTS = 256;
+// kappa * u above which a point goes to the FP64 pass: the planned refinement
 // would contract by less than 4 per step
 constexpr double FB_KU = 1.0 / 32.0;
 
@@ -94,16 +91,15 @@ static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool 
 }
 
 static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, LancLayout &L, bool on_host,
-                        bool fp32, int slots = 0, bool ds = false) {
+                        bool fp32, int slots = 0) {
     L.fp32 = fp32;
-    L.ds = ds && !fp32;
     L.mmax = o->maxiter_lanczos;
     L.S = slots > 0 ? (int)std::min<int64_t>(slots, npts) : choose_slots(h, o, npts, L.fp32, L.mmax);
     L.F = 2 * L.S;
     const size_t n = h->n, S = L.S, F = L.F, esz = L.fp32 ? sizeof(float2) : sizeof(double2);
     L.Q = c.take((size_t)(L.mmax + 1) * n * S * esz);
     L.W = c.take(n * S * esz);
-    L.xs = c.take(L.ds ? trsv_ds_scratch_bytes(h->n_pad, S) : trsv_scratch_bytes(L.fp32 ? 1 : 0, h->n_pad, S));
+    L.xs = c.take(trsv_scratch_bytes(L.fp32 ? 1 : 0, h->n_pad, S));
     L.alpha = c.get<double>(S * L.mmax);
     L.beta = c.get<double>(S * L.mmax);
     L.svec = c.get<double>(S * L.mmax);
@@ -134,11 +130,6 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     L.fin_pt = c.get<int>(F);
     L.fin_conv = c.get<int>(F);
     L.mask = c.get<int>(F);
-    if (L.ds) {
-        L.xh = c.get<float2>(n * F);
-        L.xl = c.get<float2>(n * F);
-        L.oz = c.take(oz_scratch_bytes(h->n_pad, F));
-    }
     if (L.fp32) {
         L.X64 = c.get<double2>(n * F);
         L.R64 = c.get<double2>(n * F);
@@ -172,7 +163,7 @@ void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c,
     LancLayout L, Lfb;
     const bool mixed = o->precision == PSEUDO_MIXED;
     lanc_layout(h, o, npts, c, L, o->io_host != 0, mixed);
-    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS, true);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
 }
 
 // Refine (mixed) and finalise the P finished points held in columns [0, P)
@@ -199,7 +190,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
             const double u = solve32_unit_roundoff(h);
             for (int c = 0; c < P; ++c) {
                 sg[c] = th[c] > 0.0 ? 1.0 / std::sqrt(th[c]) : 0.0;
-                // points the double-single pass will redo whatever the refinement gives
+                // points the FP64 pass will redo whatever the refinement gives
                 // (launch_fin_scatter's test with the Lanczos value, which bounds
                 // the refined one from above) are not refined
                 const double mz = h->norm2 + std::hypot(zh[c].x, zh[c].y);
@@ -215,11 +206,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
         launch_normalize(L.X64, n, F, L.mask, s);
         cudaMemcpyAsync(L.Ufin, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
-    // Rayleigh quotient and residual of the returned vectors: double-single-
-    // accurate products on the tensor cores for the FP32 pass; FP64 products
-    // for the double-single pass, whose points are the ill-conditioned ones
-    // with strongly graded singular vectors, where an error relative to the
-    // row and column maxima would swamp sigma
+    // Rayleigh quotient and residual of the returned vectors
     const bool hp = L.fp32;
     const int kc = hp ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
     int k0 = kp_begin(h, s);
@@ -229,14 +216,14 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     h->stats.mv_M_fp64_refine += 2 * (int64_t)P;
     launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);
     // kappa * u above 1/32: the planned refinement contracts by less than 4 per step
-    launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, (L.fp32 || L.ds) ? 1 : 0,
+    launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0,
                        h->norm2, L.eps,
                        neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), FB_KU,
                        L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;
 }
 
-// The points handed to the double-single pass whose sigma_min lies below
+// The points handed to the FP64 pass whose sigma_min lies below
 // working precision: one inverse-iteration step x = N(z)^{-1} v from the
 // seeded start vector v (double-single solves, about 2^-46 relative) leaves
 // ||(T - zI) x|| / ||x|| at the rounding level there.  Since sigma_min <=
@@ -245,7 +232,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
 // level, is finished with sigma = r (an upper bound of a value no FP64 method
 // resolves further), res = r / (||T||_2 + |z|) (the relative backward error of
 // x as a null vector), every membership bit set and the PSEUDO_PT_SINGULAR
-// flag; keep[t] = 0 marks it done, 1 sends it on to the double-single inverse
+// flag; keep[t] = 0 marks it done, 1 sends it on to the FP64 inverse
 // Lanczos.
 __global__ void deep_certify_kernel(int cnt, const int *__restrict__ list, const double2 *__restrict__ zc,
                                     const double *__restrict__ r2, double norm2, double sqrt_n, const double *eps,
@@ -271,7 +258,7 @@ __global__ void deep_certify_kernel(int cnt, const int *__restrict__ list, const
     }
 }
 
-// Triage of the nfb points in L.fb_list before the double-single pass: the points
+// Triage of the nfb points in L.fb_list before the FP64 pass: the points
 // certified singular to working precision (deep_certify_kernel) are written
 // out; the others are compacted to the front of L.fb_list, in their order,
 // and nfb becomes their count.  Scratch: the main pass's Lanczos basis, free
@@ -285,7 +272,7 @@ static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, L
     const size_t per_col = 2 * (size_t)n * sizeof(double2) + (size_t)n_pad * sizeof(double2) + 64;
     int64_t tc = std::min<int64_t>(nfb, (int64_t)(qbytes / per_col) - 64);
     tc = tc / 8 * 8;
-    if (tc < 8) return 0;  // no room: every point takes the full double-single pass
+    if (tc < 8) return 0;  // no room: every point takes the full FP64 pass
     Carver c((char *)L.Q, qbytes);
     double2 *X = c.get<double2>((size_t)n * tc), *Y = c.get<double2>((size_t)n * tc);
     void *xs = c.take(trsv_ds_scratch_bytes(n_pad, tc));
@@ -352,7 +339,7 @@ static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const 
     // Rayleigh quotient error is the square of the vector error after one
     // inverse-iteration step, so 1e-9 on the Ritz value is ample for 1e-8 on sigma
     const double tol_q = L.fp32 ? 1e-9 : rt / 2.0;
-    const double tol_floor = L.fp32 ? 1e-6 : L.ds ? 1e-12 : 1e-15;
+    const double tol_floor = L.fp32 ? 1e-6 : 1e-15;
     const int passes = L.fp32 ? 1 : 2;  // Gram-Schmidt passes of the reorthogonalisation
 
     // fill every slot with a point
@@ -398,14 +385,12 @@ static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const 
         } else {
             double2 *Q = (double2 *)L.Q, *W = (double2 *)L.W;
             launch_slot_copy<double>(Q, qs, W, n, S, L.jv, L.active, s);
-            const int kcs = L.ds ? PSEUDO_K_TRSV_DS : PSEUDO_K_TRSV64;
             e = cudaSuccess;
             for (int lower = 1; lower >= 0 && e == cudaSuccess; --lower) {
                 const int k0 = kp_begin(h, s);
-                e = L.ds ? launch_trsv_ds(h, lower, L.cols, L.zslot, ncnt, L.cnt, W, S, L.xs, s)
-                         : launch_trsv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, L.cols, L.zslot, ncnt, L.cnt, W,
-                                         S, (double2 *)L.xs, s);
-                kp_end(h, k0, kcs, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
+                e = launch_trsv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, L.cols, L.zslot, ncnt, L.cnt, W, S,
+                                  (double2 *)L.xs, s);
+                kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
             }
             const int k0 = kp_begin(h, s);
             launch_slot_orth_grid<double>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, L.Hp, L.nrm2,
@@ -427,7 +412,7 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     LancLayout L, Lfb;
     const bool mixed = o->precision == PSEUDO_MIXED;
     lanc_layout(h, o, io.npts, c, L, io.on_host, mixed);
-    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS, true);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
     if (c.overflow) return set_err(PSEUDO_ERR_WORKSPACE, "workspace too small");
     const int64_t npts = io.npts;
     cudaError_t e;
@@ -457,7 +442,7 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "pseudo_grid");
     h->stats.n_fallback += nfb;
     // the points mixed precision could not vouch for: first those singular to
-    // working precision, then the rest in double-single inverse Lanczos, CH at a time
+    // working precision, then the rest in FP64 inverse Lanczos, CH at a time
     if (nfb > 0) {
         double min_level = HUGE_VAL;
         for (int i = 0; i < io.neps; ++i) min_level = std::min(min_level, io.eps_host[i]);
