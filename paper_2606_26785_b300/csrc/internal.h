@@ -152,11 +152,16 @@ template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
                          const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
                          int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
-                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s);
+                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s, const double2 *vw = nullptr,
+                         int64_t ldw = 0, const int *posw = nullptr, int offw = 0);
+// fallback points (fb_list != NULL) get column t of U0 (n x ldu) copied to
+// column k of warm (n x ldw) when warm != NULL, k = their place in fb_list
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
-                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s);
+                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s,
+                        const double2 *U0 = nullptr, int64_t ldu = 0, double2 *warm = nullptr, int64_t ldw = 0,
+                        int n = 0, const double2 *v0 = nullptr);
 void launch_fb_gather(const int *list, int cnt, const double2 *zall, double2 *zc, cudaStream_t s);
 void launch_fb_scatter(const int *list, int cnt, const double *sc, const double *rc, const int32_t *fc,
                        const uint32_t *mc, double *sigma, double *res, int32_t *flags, uint32_t *member,

@@ -53,6 +53,12 @@ struct LancLayout {
     // mixed precision: points redone in the FP64 pass (list, count) and the compact
     // per-chunk arrays of that pass (capacity CH)
     int *fb_list = nullptr, *fb_cnt = nullptr;
+    // the Ritz vectors of the points handed to the FP64 pass (n x W, column k
+    // for fb_list entry k), their copy point U0 (n x F), and after the triage
+    // the original fb_list position of each kept point (fb_pos)
+    double2 *U0 = nullptr, *warm = nullptr;
+    int64_t ldwarm = 0;
+    int *fb_pos = nullptr;
     int CH = 0;
     double2 *fb_z = nullptr;
     double *fb_sig = nullptr, *fb_res = nullptr;
@@ -143,6 +149,12 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
         L.perm = c.get<int>(F);
         L.fb_list = c.get<int>(npts);
         L.fb_cnt = c.get<int>(4);
+        L.fb_pos = c.get<int>(npts);
+        if ((double)n * npts * sizeof(double2) <= 16e9) {  // warm starts for the FP64 pass
+            L.ldwarm = npts;
+            L.U0 = c.get<double2>(n * F);
+            L.warm = c.get<double2>(n * (size_t)npts);
+        }
         L.CH = 4 * FB_SLOTS;
         L.fb_z = c.get<double2>(L.CH);
         L.fb_sig = c.get<double>(L.CH);
@@ -175,6 +187,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     launch_fill_int(L.mask, F, 0, s);
     launch_fill_int(L.mask, P, 1, s);
     launch_normalize(L.Ufin, n, F, L.mask, s);
+    if (L.fp32 && L.warm) cudaMemcpyAsync(L.U0, L.Ufin, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     if (L.fp32) {
         IRBufs ib{L.R64, L.D32, L.rn2, L.mask, L.need, L.perm, L.xs32, L.xh, L.xl, L.oz};
         IRPlan plan;
@@ -219,7 +232,8 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0,
                        h->norm2, L.eps,
                        neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), FB_KU,
-                       L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s);
+                       L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s, L.U0, F, L.fp32 ? L.warm : nullptr, L.ldwarm, n,
+                       L.startv);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;
 }
 
@@ -265,7 +279,8 @@ __global__ void deep_certify_kernel(int cnt, const int *__restrict__ list, const
 // by now.  Returns 0, or an error code.
 static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, LancLayout &Lfb, const double2 *zall,
                            int neps, double min_level, double *sig_all, double *res_all, int32_t *flags_all,
-                           uint32_t *member_all, int &nfb, cudaStream_t s) {
+                           uint32_t *member_all, int &nfb, bool &compacted, cudaStream_t s) {
+    compacted = false;
     const int n = h->n, n_pad = h->n_pad;
     const size_t qbytes = (size_t)(L.mmax + 1) * n * L.S * (L.fp32 ? sizeof(float2) : sizeof(double2));
     // per column: x, (T - zI) x, solve scratch, shift, norm, flag, list entry (+ slack for alignment)
@@ -280,8 +295,9 @@ static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, L
     double *r2 = c.get<double>(tc);
     int *keep = c.get<int>(tc);
     if (c.overflow) return 0;
-    std::vector<int> list_h(nfb), keep_h(tc), kept;
+    std::vector<int> list_h(nfb), keep_h(tc), kept, kept_pos;
     kept.reserve(nfb);
+    kept_pos.reserve(nfb);
     cudaMemcpyAsync(list_h.data(), L.fb_list, nfb * sizeof(int), cudaMemcpyDeviceToHost, s);
     launch_start_vector(Lfb.startv, n, o->seed, s);
     cudaError_t e = cudaSuccess;
@@ -309,15 +325,23 @@ static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, L
         cudaMemcpyAsync(keep_h.data(), keep, cnt * sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback triage");
         for (int t = 0; t < cnt; ++t) {
-            if (keep_h[t]) kept.push_back(list_h[off + t]);
-            else ++nsing;
+            if (keep_h[t]) {
+                kept.push_back(list_h[off + t]);
+                kept_pos.push_back(off + t);
+            } else {
+                ++nsing;
+            }
         }
         h->stats.sv_R += 2 * (int64_t)cnt;
         h->stats.mv_M_fp64_refine += cnt;
     }
-    if (!kept.empty()) cudaMemcpyAsync(L.fb_list, kept.data(), kept.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    if (!kept.empty()) {
+        cudaMemcpyAsync(L.fb_list, kept.data(), kept.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(L.fb_pos, kept_pos.data(), kept_pos.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "fallback triage");
     nfb = (int)kept.size();
+    compacted = true;
     h->stats.n_singular += nsing;
     return 0;
 }
@@ -325,7 +349,8 @@ static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, L
 // Continuous-batching Lanczos over the npts points zall (device) with the
 // outputs in the same order; eps levels must already be in L.eps.
 static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const double2 *zall, int64_t npts, int neps,
-                      double *sig_all, double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s) {
+                      double *sig_all, double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s,
+                      const double2 *vw = nullptr, int64_t ldw = 0, const int *posw = nullptr, int offw = 0) {
     const int n = h->n, S = L.S;
     const int64_t qs = (int64_t)n * S;
     cudaError_t e;
@@ -352,7 +377,7 @@ static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const 
         else
             launch_slot_harvest<double>((double2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd,
                                         L.pt, L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
-                                        L.fin_theta, L.fin_conv, L.startv, L.hwork, s);
+                                        L.fin_theta, L.fin_conv, L.startv, L.hwork, s, vw, ldw, posw, offw);
     };
     harvest();
     int host[4];
@@ -443,17 +468,21 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     h->stats.n_fallback += nfb;
     // the points mixed precision could not vouch for: first those singular to
     // working precision, then the rest in FP64 inverse Lanczos, CH at a time
+    bool compacted = false;
     if (nfb > 0) {
         double min_level = HUGE_VAL;
         for (int i = 0; i < io.neps; ++i) min_level = std::min(min_level, io.eps_host[i]);
-        rc = fallback_triage(h, o, L, Lfb, zall, io.neps, min_level, sig_all, res_all, flags_all, member_all, nfb, s);
+        rc = fallback_triage(h, o, L, Lfb, zall, io.neps, min_level, sig_all, res_all, flags_all, member_all, nfb,
+                             compacted, s);
         if (rc < 0) return rc;
     }
     for (int off = 0; off < nfb; off += L.CH) {
         const int cnt = std::min(L.CH, nfb - off);
         if (io.neps > 0) cudaMemcpyAsync(Lfb.eps, L.eps, io.neps * sizeof(double), cudaMemcpyDeviceToDevice, s);
         launch_fb_gather(L.fb_list + off, cnt, zall, L.fb_z, s);
-        rc = run_points(h, o, Lfb, L.fb_z, cnt, io.neps, L.fb_sig, L.fb_res, L.fb_flags, L.fb_member, s);
+        // each point's FP64 recurrence starts from its FP32 Ritz vector
+        rc = run_points(h, o, Lfb, L.fb_z, cnt, io.neps, L.fb_sig, L.fb_res, L.fb_flags, L.fb_member, s, L.warm, L.ldwarm,
+                        compacted ? L.fb_pos : nullptr, off);
         if (rc < 0) return rc;
         launch_fb_scatter(L.fb_list + off, cnt, L.fb_sig, res_all ? L.fb_res : nullptr, L.fb_flags,
                           L.fb_member, sig_all, res_all, flags_all, member_all, s);

@@ -596,15 +596,25 @@ slot_ritz_kernel(const cx_t<real> *__restrict__ Q, int64_t qs, int n, int S, int
     }
 }
 
-// Start vectors of the refilled slots.
+// Start vectors of the refilled slots: the common seeded vector v0, or, when
+// vw is given, the point's own unit start vector, column posw[offw + pt] (or
+// offw + pt) of the row-major n x ldw array vw.
 template <typename real>
 __global__ void __launch_bounds__(256)
 slot_refill_kernel(cx_t<real> *__restrict__ Q, int n, int S, const int4 *__restrict__ work, const int *__restrict__ cnt,
-                   const double2 *__restrict__ v0) {
+                   const double2 *__restrict__ v0, const int *__restrict__ pt, const double2 *__restrict__ vw,
+                   int64_t ldw, const int *__restrict__ posw, int offw) {
     const int64_t total = (int64_t)(*cnt) * n;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int c = work[w / n].x, i = (int)(w % n);
-        Q[(int64_t)i * S + c] = mk<real>((real)v0[i].x, (real)v0[i].y);
+        double2 v;
+        if (vw) {
+            const int k = offw + pt[c];
+            v = vw[(int64_t)i * ldw + (posw ? posw[k] : k)];
+        } else {
+            v = v0[i];
+        }
+        Q[(int64_t)i * S + c] = mk<real>((real)v.x, (real)v.y);
     }
 }
 
@@ -616,7 +626,9 @@ __global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const 
                                    double norm2, const double *__restrict__ eps, int neps, double *__restrict__ sigma_out,
                                    double *__restrict__ res_out, int32_t *__restrict__ flags_out,
                                    uint32_t *__restrict__ member_out, int *__restrict__ nbad, double u_solve,
-                                   double fb_ku, int *__restrict__ fb_list, int *__restrict__ fb_cnt) {
+                                   double fb_ku, int *__restrict__ fb_list, int *__restrict__ fb_cnt,
+                                   const double2 *__restrict__ U0, int64_t ldu, double2 *__restrict__ warm,
+                                   int64_t ldw, int n, const double2 *__restrict__ v0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= P) return;
     const double th = fin_theta[t];
@@ -632,7 +644,14 @@ __global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const 
         // of the solves stops contracting; such points are redone in FP64
         const double sg = fmin(sig, sl > 0.0 ? sl : sig);
         if (!fin_conv[t] || !(sg > 0.0) || (mz / sg) * u_solve > fb_ku) {
-            fb_list[atomicAdd(fb_cnt, 1)] = g;
+            const int k = atomicAdd(fb_cnt, 1);
+            fb_list[k] = g;
+            // the point's (unit) Ritz vector starts its FP64 recurrence; a point
+            // whose FP32 recurrence broke down starts from the common vector v0
+            if (warm) {
+                const bool good = isfinite(th) && th > 0.0;
+                for (int i = 0; i < n; ++i) warm[(int64_t)i * ldw + k] = good ? U0[(int64_t)i * ldu + t] : v0[i];
+            }
             return;
         }
     }
@@ -673,7 +692,8 @@ template <typename real>
 void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, const double *svec, int *jv, int *active,
                          const double *theta, const int *convd, int *pt, double2 *zslot, const double2 *zall, int npts,
                          int *counters, double2 *Ufin, int F, int *fin_pt, double2 *fin_z, double *fin_theta,
-                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s) {
+                         int *fin_conv, const double2 *v0, int4 *work, cudaStream_t s, const double2 *vw,
+                         int64_t ldw, const int *posw, int offw) {
     cudaMemsetAsync(counters + 2, 0, 2 * sizeof(int), s);
     note_launch();
     slot_book_kernel<<<(S + 255) / 256, 256, 0, s>>>(S, jv, active, theta, convd, pt, zslot, zall, npts, counters,
@@ -684,17 +704,18 @@ void launch_slot_harvest(cx_t<real> *Q, int64_t qs, int n, int S, int mmax, cons
     note_launch();
     slot_ritz_kernel<real><<<nsm * 8, 256, 0, s>>>(Q, qs, n, S, mmax, svec, work, counters + 2, Ufin, F);
     note_launch();
-    slot_refill_kernel<real><<<nsm * 8, 256, 0, s>>>(Q, n, S, work + S, counters + 3, v0);
+    slot_refill_kernel<real><<<nsm * 8, 256, 0, s>>>(Q, n, S, work + S, counters + 3, v0, pt, vw, ldw, posw, offw);
 }
 void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const double *fin_theta, const int *fin_conv,
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
-                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s) {
+                        double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s, const double2 *U0,
+                        int64_t ldu, double2 *warm, int64_t ldw, int n, const double2 *v0) {
     if (P > 0) {
         note_launch(); fin_scatter_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, fin_pt, fin_z, fin_theta, fin_conv, s2, rr, use_rq, norm2,
                                                                         eps, neps, sigma_out, res_out, flags_out,
                                                                         member_out, nbad, u_solve, fb_ku, fb_list,
-                                                                        fb_cnt);
+                                                                        fb_cnt, U0, ldu, warm, ldw, n, v0);
     }
 }
 
@@ -734,11 +755,12 @@ template void launch_slot_orth<double>(double2 *, int64_t, double2 *, int, int, 
                                        double *, int, cudaStream_t);
 template void launch_slot_harvest<float>(float2 *, int64_t, int, int, int, const double *, int *, int *, const double *,
                                          const int *, int *, double2 *, const double2 *, int, int *, double2 *, int,
-                                         int *, double2 *, double *, int *, const double2 *, int4 *, cudaStream_t);
+                                         int *, double2 *, double *, int *, const double2 *, int4 *, cudaStream_t,
+                                         const double2 *, int64_t, const int *, int);
 template void launch_slot_harvest<double>(double2 *, int64_t, int, int, int, const double *, int *, int *,
                                           const double *, const int *, int *, double2 *, const double2 *, int, int *,
                                           double2 *, int, int *, double2 *, double *, int *, const double2 *, int4 *,
-                                          cudaStream_t);
+                                          cudaStream_t, const double2 *, int64_t, const int *, int);
 
 }  // namespace pseudo
 
