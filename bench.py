@@ -328,6 +328,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison paths and the CPU baseline")
+    ap.add_argument("--recycle-ranks", default="32",
+                    help="recycled ranks k of the Toeplitz recycling comparison (comma-separated; 8,32,64 for all "
+                         "three, about 140 s each)")
     ap.add_argument("--extras-budget", type=float, default=480.0,
                     help="seconds of wall time the comparison paths may take; the ones that would start later are "
                          "reported as skipped")
@@ -581,7 +584,8 @@ def main():
             t_ex = time.time()
             for name, fn in (("gaussian2000_invlanc_mixed", lambda: gaussian_line(p, torch, eps)),
                              ("multi_matrix_64", lambda: multi_line(64, 2, 1)),
-                             ("toeplitz_recycling", lambda: toeplitz_recycling(p, torch, eps))):
+                             ("toeplitz_recycling", lambda: toeplitz_recycling(
+                                 p, torch, eps, [int(k) for k in args.recycle_ranks.split(",")]))):
                 if time.time() - t_ex > args.extras_budget:
                     extras[name] = {"skipped": f"comparison budget of {args.extras_budget:.0f} s spent"}
                     continue
@@ -639,12 +643,12 @@ def gaussian_line(p, torch, eps):
 TOEPLITZ_GOLDEN = ROOT / "tests" / "golden" / "toeplitz1200_samples.json"
 
 
-def toeplitz_recycling(p, torch, eps):
+def toeplitz_recycling(p, torch, eps, ranks=(8, 32, 64)):
     """The recycled Rayleigh--Ritz-SVD path (Alg. 3) next to inverse Lanczos on
     the banded Toeplitz + noise matrix (superdiagonal 1, subdiagonal 0.25,
     complex Gaussian noise 1e-3/sqrt(n), seed 5) at n = 1200 on a 50 x 50 grid
     over the workload's window [-1.5, 1.5] x [-1, 1], in mixed precision at
-    recycled ranks k = 8, 32, 64 (r = 4): acceptance counts, points/s, the
+    the given recycled ranks k (r = 4): acceptance counts, points/s, the
     agreement of every converged result with inverse Lanczos, and the stored
     oracle values (tests/golden/toeplitz1200_samples.json) at the points
     reported converged."""
@@ -688,7 +692,7 @@ def toeplitz_recycling(p, torch, eps):
     o_inv = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
     h.grid(zt[:64], eps, opts=o_inv)
     s_ref, f_ref = run("invlanc_mixed", o_inv)
-    for k in (8, 32, 64):
+    for k in ranks:
         o = p.default_opts(mode=p.RECYCLE, precision=p.MIXED, rtol=1e-8, r=4, p_max=k // 4, grid_nx=nx, grid_ny=ny,
                            batch_b=20)
         sig, fl = run(f"recycle_mixed_k{k}", o)

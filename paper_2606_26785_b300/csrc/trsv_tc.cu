@@ -133,6 +133,9 @@ namespace {
 #ifndef TC_PD
 #define TC_PD 4   // prefetch distance of the diagonal-block coefficients (steps)
 #endif
+#ifndef TC_A_EVICT_LAST
+#define TC_A_EVICT_LAST 1   // A chunks copied with an L2 evict-last policy (every CTA streams them)
+#endif
 constexpr int NS = TC_NS, TC_THREADS = 256;
 constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
 
@@ -256,7 +259,10 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                     if (q >= NS && !wait_or_abort(&freeb[st], ((q / NS) - 1) & 1, &s_abort, wait_ns)) { ok = false; break; }
                     float *dst = sbuf + st * STAGE_F;
                     tc::mbar_expect_tx(&full[st], (uint32_t)L::stage);
-                    tc::bulk_g2s_hint(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st], keep);
+                    if (TC_A_EVICT_LAST)
+                        tc::bulk_g2s_hint(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st], keep);
+                    else
+                        tc::bulk_g2s(dst, Ap + (int64_t)t * A_CHUNK, A_CHUNK * sizeof(float), &full[st]);
                     tc::bulk_g2s(dst + A_CHUNK, bimg + (int64_t)(k0 / KC) * L::B_IMG, L::B_IMG * sizeof(float),
                                  &full[st]);
                     s_last_ld = q;
