@@ -118,6 +118,11 @@ typedef struct {
                            choice of the library's tuned table for the matrix order
                            (pseudo_tuned_config) */
     int traversal;      /* RECYCLE on a Cartesian grid: the visiting order, PSEUDO_TRAVERSE_* */
+    int device_loop;    /* INVLANC: 1 (default) = the Lanczos driver's loop runs on the device,
+                           captured once per call as a CUDA graph whose conditional nodes
+                           decide every step, finish and stop (no host round trip per step);
+                           0 = the host reads the slot counts back after every step.  Kernel
+                           profiling (profile = 1) always takes the host loop. */
 } pseudo_opts;
 
 typedef struct {
@@ -136,6 +141,10 @@ typedef struct {
     int64_t n_singular;  /* of those, points found singular to working precision (PSEUDO_PT_SINGULAR) */
     int64_t n_rtilde_capped; /* recycle mode: recySing evaluations whose r~ of eq. (tau) exceeded the
                                 16 columns the second Rayleigh--Ritz step keeps */
+    int64_t n_graph_launches; /* launches of the device-driven Lanczos loop's graph (device_loop) */
+    int64_t n_graph_builds;   /* of those graphs, captured and instantiated (the others were cached:
+                                 a call with the same workspace, inputs, outputs and options) */
+    double ms_graph_build;    /* host time spent capturing and instantiating them */
 } pseudo_stats_t;
 
 /* Per-kernel-class accounting (filled when pseudo_opts.profile = 1): launches,
@@ -151,6 +160,7 @@ enum {
     PSEUDO_K_RECYSING,    /* recycled Rayleigh--Ritz-SVD + residual, one CTA per point */
     PSEUDO_K_LANCZOS,     /* Lanczos reorthogonalisation */
     PSEUDO_K_TRSV_DS,     /* multi-shift triangular solve, double-single on FP32 units */
+    PSEUDO_K_RECT_QR,     /* rectangular pencil: per-point QR of [T - zI; B], FP64 */
     PSEUDO_K_COUNT
 };
 typedef struct {
@@ -162,16 +172,27 @@ int pseudo_kernel_stats(pseudo_handle h, int kclass, pseudo_kstat *out);
 /* Fill *o with defaults. Returns PSEUDO_OK or PSEUDO_ERR_ARG (o == NULL). */
 int pseudo_opts_default(pseudo_opts *o);
 
-/* Create a handle from the upper-triangular Schur factor T (SM2.1: M = T, S = I).
- *   T         : column-major complex n x n with leading dimension ldT >= m;
- *               only the upper triangle (i <= j) is read.
+/* Create a handle from the output of the preliminary reduction (SM2).
+ * Square C (SM2.1: M = T, S = I): m = n, T is the upper-triangular Schur factor.
+ * Rectangular C with m_C >= 2n rows (SM2.2: M = [C_u; R_l], S = [I; 0]): m = 2n,
+ *   rows 0..n-1 hold an upper-triangular T and rows n..2n-1 an upper-triangular
+ *   B such that [T - zI; B] has the singular values of C - zI for every z (for
+ *   example T = U^H C_u U from the Schur form of the top block and B the
+ *   triangular factor of R_l U; the host reduction of the package's workloads
+ *   module computes them).  Such a handle runs mode INVLANC in precision FP64
+ *   only: every point factors its own pencil (Alg. 3's QR of eq. (triGen)).
+ *   T         : column-major complex m x n with leading dimension ldT >= m;
+ *               only the upper triangle of each n x n block (i <= j) is read.
  *   t_on_host : 1 if T is host memory, 0 if device memory.
- *   m, n      : must be equal (rectangular input -> PSEUDO_ERR_UNSUPPORTED).
+ *   m, n      : m = n or m = 2n (any other m -> PSEUDO_ERR_UNSUPPORTED; m = 2n
+ *               needs n <= 14000, else UNSUPPORTED).
  *   stream    : cudaStream_t for the set-up copies/kernels.
- * The library copies T into handle-owned device buffers (packed FP64 and FP32
- * panels of T and T^H) -- the only device allocations the library makes; the
- * caller may free T on return.  Also computes ||T||_F and a 2-norm estimate.
- * Errors: ARG (null/size), UNSUPPORTED (m != n), NONFINITE, CUDA. */
+ * The library copies T (and B) into handle-owned device buffers (packed FP64
+ * and FP32 panels of T and T^H; for m = 2n also FP64 panels of B and B^H and
+ * the dense 2n x n pencil) -- the only device allocations the library makes;
+ * the caller may free T on return.  Also computes ||M||_F and a 2-norm
+ * estimate of M.  Errors: ARG (null/size), UNSUPPORTED (m not n or 2n),
+ * NONFINITE, CUDA. */
 int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_on_host,
                   void *stream, pseudo_handle *out);
 
@@ -276,6 +297,7 @@ const char *pseudo_last_error(void);
 int64_t pseudo_launch_count(void);
 
 /* ---- kernel-level entry points (used by the tests; same rules as above) ----
+ * All three need a square handle (m = n); a rectangular one gives UNSUPPORTED.
  *
  * pseudo_solve: X[:, c] <- (T - z_c I)^{-1} X[:, c] (adjoint = 0) or
  *               (T - z_c I)^{-H} X[:, c] (adjoint = 1) for c < ncols: the

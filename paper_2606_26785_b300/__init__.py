@@ -15,7 +15,7 @@ from ._abi import (  # noqa: F401
     DOUBLE_SINGLE, FP64, INVLANC, MIXED, MIXED_CUDACORE, RECYCLE, TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON, Opts,
     PseudoError, Stats, check)
 
-__all__ = ["Pseudo", "grid_batch", "traversal_order", "tuned_config", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE",
+__all__ = ["Pseudo", "grid_batch", "grid_batch_workspace_bytes", "traversal_order", "tuned_config", "default_opts", "FP64", "MIXED", "MIXED_CUDACORE",
            "DOUBLE_SINGLE", "INVLANC",
            "RECYCLE", "TRAVERSE_BATCH_ZIGZAG", "TRAVERSE_HILBERT", "TRAVERSE_MORTON", "PseudoError"]
 
@@ -47,7 +47,9 @@ def _stream_ptr(stream):
 
 
 class Pseudo:
-    """Handle on one Schur factor T (n x n, upper triangular, complex128)."""
+    """Handle on one Schur factor T (n x n, upper triangular, complex128), or
+    on a rectangular pencil [T; B] (2n x n, both blocks upper triangular; see
+    ``workloads.rect_reduce``)."""
 
     def __init__(self, T, stream=None):
         torch = _torch()
@@ -56,12 +58,13 @@ class Pseudo:
             Tt = torch.from_numpy(np.asfortranarray(T.astype(np.complex128)).T.copy()).cuda()
         else:
             Tt = T.to(device="cuda", dtype=torch.complex128).t().contiguous()
-        # Tt holds T^T row-major == T column-major
-        n = Tt.shape[0]
+        # Tt holds T^T row-major == T column-major (m x n, leading dimension m)
+        n, m = Tt.shape
         h = ctypes.c_void_p()
-        check(lib.pseudo_create(_ptr(Tt), n, n, n, 0, _stream_ptr(stream), ctypes.byref(h)))
+        check(lib.pseudo_create(_ptr(Tt), m, m, n, 0, _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
         self.n = n
+        self.m = m
         self._lib = lib
 
     def close(self):
@@ -107,18 +110,26 @@ class Pseudo:
         check(self._lib.pseudo_workspace_bytes(self._h, ctypes.byref(opts), int(npts), ctypes.byref(b)))
         return b.value
 
-    def grid(self, z, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, **kw):
+    def grid(self, z, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, out=None, **kw):
         """sigma_min(T - z I) for a 1-D complex128 CUDA tensor (or array) z.
-        Returns dict of CUDA tensors: sigma, res, flags, member, plus 'status'."""
+        Returns dict of CUDA tensors: sigma, res, flags, member, plus 'status'.
+        ``out``: a dict returned by an earlier call on as many points, whose
+        tensors receive the results (with the same workspace, a repeated call
+        then replays the library's cached loop graph)."""
         torch = _torch()
         o = opts if opts is not None else default_opts(**kw)
         zt = torch.as_tensor(np.asarray(z, dtype=np.complex128)) if not torch.is_tensor(z) else z
         zt = zt.to(device="cuda", dtype=torch.complex128).contiguous()
         npts = zt.numel()
-        sigma = torch.empty(npts, dtype=torch.float64, device="cuda")
-        res = torch.empty(npts, dtype=torch.float64, device="cuda")
-        flags = torch.empty(npts, dtype=torch.int32, device="cuda")
-        member = torch.zeros(npts, dtype=torch.int32, device="cuda")
+        if out is not None:
+            sigma, res, flags, member = out["sigma"], out["res"], out["flags"], out["member"]
+            assert all(t.numel() == npts and t.is_cuda for t in (sigma, res, flags, member))
+            member.zero_()
+        else:
+            sigma = torch.empty(npts, dtype=torch.float64, device="cuda")
+            res = torch.empty(npts, dtype=torch.float64, device="cuda")
+            flags = torch.empty(npts, dtype=torch.int32, device="cuda")
+            member = torch.zeros(npts, dtype=torch.int32, device="cuda")
         eps = np.ascontiguousarray(np.asarray(eps_levels, dtype=np.float64))
         need = self.workspace_bytes(npts, o)
         if workspace is None or workspace.numel() < need:
@@ -214,10 +225,12 @@ class Pseudo:
         return Y
 
 
-def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, **kw):
+def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=None, stream=None, out=None, **kw):
     """sigma_min for many matrices at once: handles[m] (distinct Pseudo
     objects) on the complex128 grid zs[m].  The matrices run concurrently on
-    the device.  Returns (list of per-matrix dicts as Pseudo.grid, status)."""
+    the device.  Returns (list of per-matrix dicts as Pseudo.grid, status).
+    ``out``: the list an earlier call returned, whose tensors receive the
+    results (as in Pseudo.grid)."""
     torch = _torch()
     lib = _abi.load()
     o = Opts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
@@ -227,13 +240,19 @@ def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=N
         raise ValueError("need one grid per handle")
     zt = [(z if torch.is_tensor(z) else torch.as_tensor(np.asarray(z, dtype=np.complex128)))
           .to(device="cuda", dtype=torch.complex128).contiguous() for z in zs]
-    outs = []
-    for z in zt:
-        k = z.numel()
-        outs.append({"sigma": torch.empty(k, dtype=torch.float64, device="cuda"),
-                     "res": torch.empty(k, dtype=torch.float64, device="cuda"),
-                     "flags": torch.empty(k, dtype=torch.int32, device="cuda"),
-                     "member": torch.zeros(k, dtype=torch.int32, device="cuda")})
+    if out is not None:
+        outs = out
+        assert len(outs) == nmat and all(o_["sigma"].numel() == z.numel() for o_, z in zip(outs, zt))
+        for o_ in outs:
+            o_["member"].zero_()
+    else:
+        outs = []
+        for z in zt:
+            k = z.numel()
+            outs.append({"sigma": torch.empty(k, dtype=torch.float64, device="cuda"),
+                         "res": torch.empty(k, dtype=torch.float64, device="cuda"),
+                         "flags": torch.empty(k, dtype=torch.int32, device="cuda"),
+                         "member": torch.zeros(k, dtype=torch.int32, device="cuda")})
     hs = (ctypes.c_void_p * nmat)(*[h._h.value for h in handles])
     npts = (ctypes.c_int64 * nmat)(*[z.numel() for z in zt])
 
@@ -251,6 +270,18 @@ def grid_batch(handles, zs, eps_levels=(), opts: Opts | None = None, workspace=N
         ctypes.byref(o), ptrs("sigma"), ptrs("res"), ptrs("flags"), ptrs("member"), _ptr(workspace),
         workspace.numel(), _stream_ptr(stream)))
     return outs, rc
+
+
+def grid_batch_workspace_bytes(handles, npts, opts: Opts) -> int:
+    """Device workspace bytes grid_batch needs (pseudo_grid_batch_workspace_bytes)."""
+    nmat = len(handles)
+    hs = (ctypes.c_void_p * nmat)(*[h._h.value for h in handles])
+    np_ = (ctypes.c_int64 * nmat)(*[int(k) for k in npts])
+    o = Opts.from_buffer_copy(opts)
+    o.io_host = 0
+    need = ctypes.c_size_t()
+    check(_abi.load().pseudo_grid_batch_workspace_bytes(hs, nmat, np_, ctypes.byref(o), ctypes.byref(need)))
+    return need.value
 
 
 def tuned_config(n: int) -> dict:

@@ -32,7 +32,7 @@ class Opts(ctypes.Structure):
         ("omega", ctypes.c_double), ("eta", ctypes.c_double), ("rtol", ctypes.c_double),
         ("maxiter_lanczos", ctypes.c_int), ("maxiter_lobpcg", ctypes.c_int), ("max_ir", ctypes.c_int),
         ("io_host", ctypes.c_int), ("seed", ctypes.c_uint64), ("profile", ctypes.c_int), ("fp32_solver", ctypes.c_int),
-        ("traversal", ctypes.c_int),
+        ("traversal", ctypes.c_int), ("device_loop", ctypes.c_int),
     ]
 
 
@@ -41,14 +41,17 @@ class KStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos", "trsv_ds")
+KCLASSES = ("trsv32", "trsv64", "trmv64", "trmv_ds", "recysing", "lanczos", "trsv_ds", "rect_qr")
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "sv_R", "mv_M", "mv_M_fp64_refine", "n_points", "n_accepted", "n_refined", "n_not_converged",
         "n_updates", "lanczos_steps", "lobpcg_iters", "n_fallback")] + [(k, ctypes.c_double) for k in (
-        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")] + [("n_singular", ctypes.c_int64), ("n_rtilde_capped", ctypes.c_int64)]
+        "ms_recysing", "ms_refine", "ms_update", "ms_polish", "ms_total")] + [("n_singular", ctypes.c_int64), ("n_rtilde_capped", ctypes.c_int64),
+                                                       ("n_graph_launches", ctypes.c_int64),
+                                                       ("n_graph_builds", ctypes.c_int64),
+                                                       ("ms_graph_build", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -84,14 +84,14 @@ normalize_kernel(double2 *__restrict__ X, int n, int S, const int *__restrict__ 
 //   s2 = ||Y||^2 (Rayleigh quotient of N(z) at x), r = ||NX - s2 x||.
 __global__ void __launch_bounds__(CW * 32)
 rq_residual_kernel(const double2 *__restrict__ U, const double2 *__restrict__ Y, const double2 *__restrict__ NX, int n,
-                   int S, const int *__restrict__ mask, double *__restrict__ s2_out, double *__restrict__ r_out) {
+                   int ny, int S, const int *__restrict__ mask, double *__restrict__ s2_out, double *__restrict__ r_out) {
     __shared__ double sh[CW][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * 32 + lane;
     const bool on = c < S && (!mask || mask[c]);
     double s = 0.0;
     if (on)
-        for (int i = warp; i < n; i += CW) { const double2 v = Y[(int64_t)i * S + c]; s += v.x * v.x + v.y * v.y; }
+        for (int i = warp; i < ny; i += CW) { const double2 v = Y[(int64_t)i * S + c]; s += v.x * v.x + v.y * v.y; }
     const double s2 = block_col_sum(s, sh);
     double r = 0.0;
     if (on)
@@ -157,8 +157,8 @@ void launch_normalize(double2 *X, int n, int S, const int *mask, cudaStream_t s)
     note_launch(); normalize_kernel<<<cgroups(S), CW * 32, 0, s>>>(X, n, S, mask);
 }
 void launch_rq_residual(const double2 *U, const double2 *Y, const double2 *NX, int n, int S, const int *mask,
-                        double *s2, double *r, cudaStream_t s) {
-    note_launch(); rq_residual_kernel<<<cgroups(S), CW * 32, 0, s>>>(U, Y, NX, n, S, mask, s2, r);
+                        double *s2, double *r, cudaStream_t s, int ny) {
+    note_launch(); rq_residual_kernel<<<cgroups(S), CW * 32, 0, s>>>(U, Y, NX, n, ny > 0 ? ny : n, S, mask, s2, r);
 }
 void launch_finalize(int S, int64_t w0, const double2 *z, const double *theta, const double *s2, const double *rr,
                      const int *active, const int *extra_flags, int sig_src, double norm2, const double *eps, int neps,

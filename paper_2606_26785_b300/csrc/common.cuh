@@ -11,6 +11,10 @@ namespace pseudo {
 
 // Counts every kernel launch the library makes (process-wide).
 void note_launch();
+// kernels run by graph replays (counted on the device), and this thread's
+// running count of note_launch calls (kernels per captured graph body)
+void note_launches(long long k);
+long long thread_launch_count();
 
 // Raises a kernel's dynamic shared-memory limit before its first launch on
 // each device (the attribute is per device; `done` holds one bit per device

@@ -8,6 +8,7 @@
 #include "internal.h"
 
 namespace pseudo {
+struct GraphCache;  // instantiated device-loop graphs of a handle (invlanc.cu)
 constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
 int set_err(int code, const char *fmt, ...);
 int cuda_err(cudaError_t e, const char *where);
@@ -70,6 +71,11 @@ struct pseudo_ctx {
     void *ozA_U = nullptr, *ozA_L = nullptr;
     int *ozE_U = nullptr, *ozE_L = nullptr;
     int fp32_solver = 0;                     // 0 tensor cores, 1 CUDA cores
+    // rectangular input (m = 2n, SM2.2): M = [T; B] dense column-major (2n x n,
+    // leading dimension 2n) and the FP64 panels of B and B^H
+    bool rect = false;
+    double2 *M64 = nullptr, *BU64 = nullptr, *BL64 = nullptr;
+    pseudo::GraphCache *graph_cache = nullptr;
     double norm_fro = 0.0, norm2 = 0.0;      // ||T||_F and a 2-norm estimate
     pseudo_stats_t stats;
 };
@@ -110,6 +116,7 @@ inline double tri_bytes(int n, int ncols, double tri_esz, double vec_esz, int nv
 }
 
 void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *plan);
+void graph_cache_free(pseudo_ctx *h);
 int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
 void recycle_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, void *plan);
 int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s);
@@ -121,19 +128,22 @@ void launch_convert_32_to_64(const float2 *a, double2 *b, int64_t cnt, cudaStrea
 namespace pseudo {
 // (T - zI)^{op} products for the refinement residuals and the recycled
 // subspace: IEEE FP64 in FP64 mode, double-single on the FP32 units in mixed
-// mode.
+// mode.  With ncols_dev the launch covers ncols columns (an upper bound) and
+// the kernels read the live count from device memory.
 // xh / xl: scratch with X's layout (leading dimension ldx) for the FP32 split
 // of X used by the double-single kernel.
 inline cudaError_t trmv_hp(pseudo_ctx *h, bool ds, int lower, const int *cols, const double2 *zc, int ncols,
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
                            int subtract, cudaStream_t s, float2 *xh = nullptr, float2 *xl = nullptr,
-                           void *oz = nullptr) {
+                           void *oz = nullptr, const int *ncols_dev = nullptr) {
     if (ds && oz && h->ozA_U)
-        return launch_trmv_oz(h, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy, subtract, oz, s);
-    if (ds)
+        return launch_trmv_oz(h, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy, subtract, oz, s, ncols_dev);
+    if (ds) {
+        if (ncols_dev) return cudaErrorInvalidValue;  // the CUDA-core double-single product takes host counts only
         return launch_trmv_ds(lower ? h->L32 : h->U32, lower ? h->L32lo : h->U32lo, h->n, h->n_pad, lower, cols, zc,
                               ncols, X, ldx, B, ldb, Y, ldy, subtract, s, xh, xl);
-    return launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, cols, zc, ncols, nullptr, X, ldx, B, ldb, Y,
+    }
+    return launch_trmv64(lower ? h->L64 : h->U64, h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, B, ldb, Y,
                          ldy, subtract, s);
 }
 }  // namespace pseudo
@@ -158,5 +168,15 @@ void ir_plan(pseudo_ctx *h, const std::vector<double> &sig, const std::vector<do
              const IRBufs &b, IRPlan &plan, cudaStream_t s, int S_total = 0, const std::vector<char> *skip = nullptr);
 cudaError_t ir_solve_cols(pseudo_ctx *h, const IRBufs &b, int lower, const double2 *zc, int S, const double2 *B,
                           double2 *X, const IRPlan &plan, cudaStream_t s);
+// The same plan made on the device for the *nfin finished columns of a
+// capacity-F buffer (Lanczos values theta, shifts z, convergence flags conv):
+// need/perm in b, cnt[0 .. max_ir] (device); stat[0] and stat[1] (device)
+// accumulate the solves and products it implies.
+void ir_plan_dev(pseudo_ctx *h, const int *nfin, int F, const double *theta, const double2 *z, const int *conv,
+                 int max_ir, double fb_ku, const IRBufs &b, int *cnt, long long *stat, cudaStream_t s);
+// Refinement under a device plan: max_ir launches of each kind whose column
+// counts come from cnt, so that the launch sequence is fixed (capturable).
+cudaError_t ir_solve_cols_dev(pseudo_ctx *h, const IRBufs &b, int lower, const double2 *zc, int S, const double2 *B,
+                              double2 *X, int max_ir, const int *cnt, cudaStream_t s);
 }  // namespace pseudo
 

@@ -14,6 +14,12 @@ int trsv_group_width(int fp32);
 size_t trsv_scratch_bytes(int fp32, int64_t n_pad, int64_t ncols);
 cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
                           int ncols, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs, cudaStream_t s);
+// The same solve when only an upper bound of the column count is known on the
+// host (the live count in *ncols_dev): the column-group widths the host
+// version picks from the count are each launched over their range of counts.
+cudaError_t launch_trsv64_bounded(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                                  int bound, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs,
+                                  cudaStream_t s);
 cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
                           int ncols, const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s);
 cudaError_t launch_trmv64(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
@@ -58,7 +64,7 @@ void launch_pack_oz(const double2 *T, int64_t ldT, int n, int n_pad, void *AU, v
                     cudaStream_t s);
 cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
-                           int subtract, void *scratch, cudaStream_t s);
+                           int subtract, void *scratch, cudaStream_t s, const int *ncols_dev = nullptr);
 }  // namespace pseudo
 
 namespace pseudo {
@@ -88,8 +94,9 @@ void launch_colnorm2(const double2 *X, int n, int S, const int *mask, double *ou
 void launch_scale_to32(const double2 *R, int n, int S, const int *mask, const double *rn2, float2 *D, cudaStream_t s);
 void launch_acc_from32(double2 *X, int n, int S, const int *mask, const double *rn2, const float2 *D, cudaStream_t s);
 void launch_normalize(double2 *X, int n, int S, const int *mask, cudaStream_t s);
+// s2 = ||Y||^2 over ny rows (0: n), r = ||NX - s2 U|| over n rows, per masked column
 void launch_rq_residual(const double2 *U, const double2 *Y, const double2 *NX, int n, int S, const int *mask,
-                        double *s2, double *r, cudaStream_t s);
+                        double *s2, double *r, cudaStream_t s, int ny = 0);
 void launch_finalize(int S, int64_t w0, const double2 *z, const double *theta, const double *s2, const double *rr,
                      const int *active, const int *extra_flags, int sig_src, double norm2, const double *eps, int neps,
                      double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int base_flags,
@@ -161,7 +168,21 @@ void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const do
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
                         double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s,
                         const double2 *U0 = nullptr, int64_t ldu = 0, double2 *warm = nullptr, int64_t ldw = 0,
-                        int n = 0, const double2 *v0 = nullptr);
+                        int n = 0, const double2 *v0 = nullptr, const int *P_dev = nullptr);
+void launch_mask_prefix(int *mask, int F, const int *P, cudaStream_t s);
+// rect.cu: rectangular input (m = 2n)
+int64_t rect_packed_size(int n);
+int rect_max_order();  // largest n of a rectangular pencil (shared-memory right-hand sides)
+cudaError_t launch_rect_qr(const pseudo_ctx *h, const int *cols, int ncols, const int *ncols_dev,
+                           const double2 *zslot, double2 *Rz, double2 *Rs, double2 *Bs, cudaStream_t s);
+cudaError_t launch_rect_solve(const pseudo_ctx *h, const double2 *Rs, int lower, const int *cols, int ncols,
+                              const int *ncols_dev, double2 *X, int64_t ldx, cudaStream_t s);
+void launch_add_cols(double2 *A, const double2 *B, int64_t cnt, cudaStream_t s);
+cudaError_t rect_normal_product(pseudo_ctx *h, const double2 *zc, int ncols, const int *ncols_dev, const double2 *X,
+                                int64_t ldx, double2 *Y, int64_t ldy, double2 *NX, double2 *Tb, cudaStream_t s);
+void launch_lanc_ctrl(const int *cnt, const int *counters, int S, const int *err, long long guard, long long *ctl,
+                      long long *stat, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hf,
+                      cudaGraphConditionalHandle hs, int graph, cudaStream_t s);
 void launch_fb_gather(const int *list, int cnt, const double2 *zall, double2 *zc, cudaStream_t s);
 void launch_fb_scatter(const int *list, int cnt, const double *sc, const double *rc, const int32_t *fc,
                        const uint32_t *mc, double *sigma, double *res, int32_t *flags, uint32_t *member,

@@ -17,7 +17,10 @@
 // to a second pass: first a one-step test for sigma below working precision
 // (fallback_triage, double-single solves), then FP64 inverse Lanczos for the
 // points it does not settle.
+#include <string.h>
+
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <vector>
 
@@ -59,6 +62,15 @@ struct LancLayout {
     double2 *U0 = nullptr, *warm = nullptr;
     int64_t ldwarm = 0;
     int *fb_pos = nullptr;
+    // device-side counts: stat[0] Lanczos steps, [1] solves, [2] refinement and
+    // Rayleigh-quotient products, [3] finished batches; ctl[0] iterations of
+    // the current graph launch; ircnt: the refinement plan's column counts
+    long long *stat = nullptr, *ctl = nullptr;
+    int *ircnt = nullptr;
+    // rectangular pencil: per-slot factors R(z) and bottom-block work copies
+    // (packed upper triangles), the shift each factor belongs to, and n x F
+    // product scratch; Y then has 2n rows
+    double2 *Rs = nullptr, *Bs = nullptr, *Rz = nullptr, *Tb = nullptr;
     int CH = 0;
     double2 *fb_z = nullptr;
     double *fb_sig = nullptr, *fb_res = nullptr;
@@ -88,8 +100,10 @@ static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool 
     int64_t S = o->shift_batch > 0 ? o->shift_batch : tuned_slots(h->n);
     S = std::min<int64_t>(S, npts);
     const double esz = fp32 ? 8.0 : 16.0;
+    // rectangular pencil: two packed triangles per slot
+    const double per_slot_rect = h->rect ? 2.0 * 16.0 * (double)rect_packed_size(h->n) : 0.0;
     while (S > 32) {
-        const double bytes = (double)h->n * S * ((mmax + 2) * esz + 2.0 * (6 * 16.0 + 3 * 8.0));
+        const double bytes = (double)h->n * S * ((mmax + 2) * esz + 2.0 * (6 * 16.0 + 3 * 8.0)) + per_slot_rect * S;
         if (bytes <= 48e9) break;
         S /= 2;
     }
@@ -98,6 +112,7 @@ static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool 
 
 static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, LancLayout &L, bool on_host,
                         bool fp32, int slots = 0) {
+    memset(&L, 0, sizeof L);  // its bytes (padding included) key the graph cache
     L.fp32 = fp32;
     L.mmax = o->maxiter_lanczos;
     L.S = slots > 0 ? (int)std::min<int64_t>(slots, npts) : choose_slots(h, o, npts, L.fp32, L.mmax);
@@ -122,11 +137,21 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     L.counters = c.get<int>(4);
     L.hwork = c.get<int4>(2 * S);
     L.nbad = c.get<int>(4);
+    L.stat = c.get<long long>(8);
+    L.ctl = c.get<long long>(2);
+    L.ircnt = c.get<int>(64);
     L.zslot = c.get<double2>(S);
     L.startv = c.get<double2>(n);
     L.Ufin = c.get<double2>(n * F);
     L.fin_z = c.get<double2>(F);
-    L.Y = c.get<double2>(n * F);
+    L.Y = c.get<double2>((h->rect ? 2 : 1) * n * F);
+    if (h->rect) {
+        const size_t psz = (size_t)rect_packed_size(h->n);
+        L.Rs = c.get<double2>(psz * S);
+        L.Bs = c.get<double2>(psz * S);
+        L.Rz = c.get<double2>(S);
+        L.Tb = c.get<double2>(n * F);
+    }
     L.NX = c.get<double2>(n * F);
     L.fin_theta = c.get<double>(F);
     L.s2 = c.get<double>(F);
@@ -179,43 +204,30 @@ void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c,
 }
 
 // Refine (mixed) and finalise the P finished points held in columns [0, P)
-// of the finished buffer.
-static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int P, int neps, double *sig_all,
+// of the finished buffer, P = counters[1] on the device; every launch covers
+// the buffer's capacity F and reads P (or the refinement plan's counts) from
+// device memory, so that the sequence is the same for any P and can be
+// captured in a graph.  Leaves counters[1] = 0.
+static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int neps, double *sig_all,
                         double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s) {
     const int n = h->n, F = L.F;
+    const int *P = L.counters + 1;
     cudaError_t e;
-    launch_fill_int(L.mask, F, 0, s);
-    launch_fill_int(L.mask, P, 1, s);
+    launch_mask_prefix(L.mask, F, P, s);
     launch_normalize(L.Ufin, n, F, L.mask, s);
     if (L.fp32 && L.warm) cudaMemcpyAsync(L.U0, L.Ufin, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     if (L.fp32) {
         IRBufs ib{L.R64, L.D32, L.rn2, L.mask, L.need, L.perm, L.xs32, L.xh, L.xl, L.oz};
-        IRPlan plan;
-        {
-            std::vector<double> th(P), sg(P);
-            std::vector<double2> zh(P);
-            std::vector<int> cv(P);
-            std::vector<char> skip(P, 0);
-            cudaMemcpyAsync(th.data(), L.fin_theta, P * sizeof(double), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(zh.data(), L.fin_z, P * sizeof(double2), cudaMemcpyDeviceToHost, s);
-            cudaMemcpyAsync(cv.data(), L.fin_conv, P * sizeof(int), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
-            const double u = solve32_unit_roundoff(h);
-            for (int c = 0; c < P; ++c) {
-                sg[c] = th[c] > 0.0 ? 1.0 / std::sqrt(th[c]) : 0.0;
-                // points the FP64 pass will redo whatever the refinement gives
-                // (launch_fin_scatter's test with the Lanczos value, which bounds
-                // the refined one from above) are not refined
-                const double mz = h->norm2 + std::hypot(zh[c].x, zh[c].y);
-                skip[c] = !cv[c] || !(sg[c] > 0.0) || (mz / sg[c]) * u > FB_KU;
-            }
-            ir_plan(h, sg, zh, o->max_ir, ib, plan, s, F, &skip);
-        }
-        if ((e = ir_solve_cols(h, ib, 1, L.fin_z, F, L.Ufin, L.X64, plan, s)) != cudaSuccess) return cuda_err(e, "refine");
+        // points the FP64 pass will redo whatever the refinement gives
+        // (launch_fin_scatter's test with the Lanczos value, which bounds the
+        // refined one from above) are not refined
+        ir_plan_dev(h, P, F, L.fin_theta, L.fin_z, L.fin_conv, o->max_ir, FB_KU, ib, L.ircnt, L.stat + 1, s);
+        if ((e = ir_solve_cols_dev(h, ib, 1, L.fin_z, F, L.Ufin, L.X64, o->max_ir, L.ircnt, s)) != cudaSuccess)
+            return cuda_err(e, "refine");
         cudaMemcpyAsync(L.B64, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
-        if ((e = ir_solve_cols(h, ib, 0, L.fin_z, F, L.B64, L.X64, plan, s)) != cudaSuccess) return cuda_err(e, "refine");
-        launch_fill_int(L.mask, F, 0, s);
-        launch_fill_int(L.mask, P, 1, s);
+        if ((e = ir_solve_cols_dev(h, ib, 0, L.fin_z, F, L.B64, L.X64, o->max_ir, L.ircnt, s)) != cudaSuccess)
+            return cuda_err(e, "refine");
+        launch_mask_prefix(L.mask, F, P, s);
         launch_normalize(L.X64, n, F, L.mask, s);
         cudaMemcpyAsync(L.Ufin, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
@@ -223,17 +235,24 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
     const bool hp = L.fp32;
     const int kc = hp ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
     int k0 = kp_begin(h, s);
-    trmv_hp(h, hp, 0, nullptr, L.fin_z, P, L.Ufin, F, nullptr, F, L.Y, F, 0, s, L.xh, L.xl, L.oz);
-    trmv_hp(h, hp, 1, nullptr, L.fin_z, P, L.Y, F, nullptr, F, L.NX, F, 0, s, L.xh, L.xl, L.oz);
-    kp_end(h, k0, kc, 2 * tri_flops(n, P), 2 * tri_bytes(n, P, 16, 16, 2), s);
-    h->stats.mv_M_fp64_refine += 2 * (int64_t)P;
-    launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s);
+    if (h->rect) {
+        // Y = M(z) x (2n rows), NX = M(z)^H Y
+        e = rect_normal_product(h, L.fin_z, F, P, L.Ufin, F, L.Y, F, L.NX, L.Tb, s);
+    } else {
+        e = trmv_hp(h, hp, 0, nullptr, L.fin_z, F, L.Ufin, F, nullptr, F, L.Y, F, 0, s, L.xh, L.xl, L.oz, P);
+        if (e == cudaSuccess)
+            e = trmv_hp(h, hp, 1, nullptr, L.fin_z, F, L.Y, F, nullptr, F, L.NX, F, 0, s, L.xh, L.xl, L.oz, P);
+    }
+    kp_end(h, k0, kc, 0.0, 0.0, s);
+    if (e != cudaSuccess) return cuda_err(e, "finish");
+    launch_rq_residual(L.Ufin, L.Y, L.NX, n, F, L.mask, L.s2, L.rr, s, h->rect ? 2 * n : n);
     // kappa * u above 1/32: the planned refinement contracts by less than 4 per step
-    launch_fin_scatter(P, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0,
+    launch_fin_scatter(F, L.fin_pt, L.fin_z, L.fin_theta, L.fin_conv, L.s2, L.rr, L.fp32 ? 1 : 0,
                        h->norm2, L.eps,
                        neps, sig_all, res_all, flags_all, member_all, L.nbad, solve32_unit_roundoff(h), FB_KU,
                        L.fp32 ? L.fb_list : nullptr, L.fb_cnt, s, L.U0, F, L.fp32 ? L.warm : nullptr, L.ldwarm, n,
-                       L.startv);
+                       L.startv, P);
+    cudaMemsetAsync(L.counters + 1, 0, sizeof(int), s);
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "finish") : 0;
 }
 
@@ -350,91 +369,369 @@ static int fallback_triage(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, L
     return 0;
 }
 
+// One Lanczos step of every running slot: two multi-shift solves, the
+// reorthogonalisation, the tridiagonal Ritz values, and the harvest (finished
+// slots to the finished buffer, refilled from the point queue).  The solves
+// cover ncols columns (the host's count, or with `bounded` the slot count S
+// as an upper bound) and read the live count L.cnt from the device.
+struct StepArgs {
+    const double2 *zall;
+    int64_t npts;
+    const double2 *vw;
+    int64_t ldw;
+    const int *posw;
+    int offw;
+    double tol_q, tol_floor;
+    int passes;
+};
+static cudaError_t lanczos_step(pseudo_ctx *h, LancLayout &L, const StepArgs &a, int ncols, cudaStream_t s,
+                                bool bounded = false) {
+    const int n = h->n, S = L.S;
+    const int64_t qs = (int64_t)n * S;
+    cudaError_t e = cudaSuccess;
+    if (L.fp32) {
+        float2 *Q = (float2 *)L.Q, *W = (float2 *)L.W;
+        launch_slot_copy<float>(Q, qs, W, n, S, L.jv, L.active, s);
+        for (int lower = 1; lower >= 0 && e == cudaSuccess; --lower) {
+            const int k0 = kp_begin(h, s);
+            e = solve32(h, lower, L.cols, L.zslot, ncols, L.cnt, W, S, (float2 *)L.xs, s);
+            kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncols), tri_bytes(n, ncols, 8, 8, 2), s);
+        }
+        const int k0 = kp_begin(h, s);
+        launch_slot_orth_grid<float>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, a.passes, L.Hp, L.nrm2,
+                                     L.alpha_acc, s);
+        kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
+    } else {
+        double2 *Q = (double2 *)L.Q, *W = (double2 *)L.W;
+        if (h->rect) {
+            // slots that got a new point since the last step factor M(z) first
+            const int k0 = kp_begin(h, s);
+            e = launch_rect_qr(h, L.cols, ncols, L.cnt, L.zslot, L.Rz, L.Rs, L.Bs, s);
+            kp_end(h, k0, PSEUDO_K_RECT_QR, 0.0, 0.0, s);
+        }
+        launch_slot_copy<double>(Q, qs, W, n, S, L.jv, L.active, s);
+        for (int lower = 1; lower >= 0 && e == cudaSuccess; --lower) {
+            const int k0 = kp_begin(h, s);
+            if (h->rect)
+                e = launch_rect_solve(h, L.Rs, lower, L.cols, ncols, L.cnt, W, S, s);
+            else if (bounded)
+                e = launch_trsv64_bounded(lower ? h->L64 : h->U64, n, h->n_pad, lower, L.cols, L.zslot, ncols, L.cnt,
+                                          W, S, (double2 *)L.xs, s);
+            else
+                e = launch_trsv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, L.cols, L.zslot, ncols, L.cnt, W, S,
+                                  (double2 *)L.xs, s);
+            kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncols), tri_bytes(n, ncols, 16, 16, 2), s);
+        }
+        const int k0 = kp_begin(h, s);
+        launch_slot_orth_grid<double>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, a.passes, L.Hp, L.nrm2,
+                                      L.alpha_acc, s);
+        kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
+    }
+    if (e != cudaSuccess) return e;
+    launch_slot_tridiag(S, L.mmax, L.alpha, L.beta, L.active, L.jv, L.theta, L.svec, L.convd, a.tol_q, a.tol_floor,
+                        L.fp32 ? 1 : 0, s);
+    if (L.fp32)
+        launch_slot_harvest<float>((float2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd, L.pt,
+                                   L.zslot, a.zall, (int)a.npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
+                                   L.fin_theta, L.fin_conv, L.startv, L.hwork, s);
+    else
+        launch_slot_harvest<double>((double2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd, L.pt,
+                                    L.zslot, a.zall, (int)a.npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
+                                    L.fin_theta, L.fin_conv, L.startv, L.hwork, s, a.vw, a.ldw, a.posw, a.offw);
+    return cudaGetLastError();
+}
+
+// Adds a conditional node (handle hc, type ty) at the capture position of the
+// capturing stream cs and returns its body graph.
+static cudaError_t capture_conditional(cudaStream_t cs, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType ty,
+                                       cudaGraph_t *body) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = ty;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &np)) != cudaSuccess) return e;
+    *body = np.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The device-driven loop: one CUDA graph whose while node runs, per
+// iteration, the compaction of the running slots, the control kernel
+// (lanc_ctrl_kernel), then under two if nodes the finish of a full finished
+// buffer (finish_batch) and one Lanczos step; the control kernel decides all
+// three on the device, so a launch runs to completion (or to the iteration
+// guard) without a host round trip.  Kernel counts per body are recorded for
+// the launch statistics.
+struct LancGraph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+    long long k_iter = 0, k_fin = 0, k_step = 0;  // kernels per iteration / finish / step
+    ~LancGraph() {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+    }
+};
+
+// Per-handle cache of instantiated loop graphs.  The key holds every value
+// the captured kernels receive (the layout's bytes, the step arguments, the
+// outputs, the options that reach a kernel), so a call whose key matches an
+// earlier one -- the same workspace, inputs and outputs, as in a serving loop
+// with preallocated buffers -- replays that graph instead of capturing and
+// instantiating a new one.  At most GRAPH_CACHE entries per handle, least
+// recently used out first.
+constexpr int GRAPH_CACHE = 4;
+struct GraphCache {
+    struct Entry {
+        std::vector<unsigned char> key;
+        LancGraph *g;
+        uint64_t used;
+    };
+    std::vector<Entry> e;
+    uint64_t tick = 0;
+    ~GraphCache() {
+        for (auto &x : e) delete x.g;
+    }
+};
+template <typename T> static void key_put(std::vector<unsigned char> &k, const T &v) {
+    const unsigned char *p = reinterpret_cast<const unsigned char *>(&v);
+    k.insert(k.end(), p, p + sizeof v);
+}
+
+static int build_lanc_graph(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const StepArgs &a, int neps,
+                            double *sig_all, double *res_all, int32_t *flags_all, uint32_t *member_all,
+                            long long guard, LancGraph &G) {
+    cudaError_t e;
+    cudaStream_t cb = nullptr, cf = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cb, cudaStreamNonBlocking)) != cudaSuccess) return cuda_err(e, "graph stream");
+    if ((e = cudaStreamCreateWithFlags(&cf, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaStreamDestroy(cb);
+        return cuda_err(e, "graph stream");
+    }
+    int rc = 0;
+    auto fail = [&](cudaError_t err, const char *where) {
+        if (!rc) rc = cuda_err(err, where);
+    };
+    do {
+        if ((e = cudaGraphCreate(&G.g, 0)) != cudaSuccess) { fail(e, "graph"); break; }
+        cudaGraphConditionalHandle hw, hf, hs;
+        if ((e = cudaGraphConditionalHandleCreate(&hw, G.g, 1, cudaGraphCondAssignDefault)) != cudaSuccess ||
+            (e = cudaGraphConditionalHandleCreate(&hf, G.g, 0, cudaGraphCondAssignDefault)) != cudaSuccess ||
+            (e = cudaGraphConditionalHandleCreate(&hs, G.g, 0, cudaGraphCondAssignDefault)) != cudaSuccess) {
+            fail(e, "graph handles");
+            break;
+        }
+        cudaMemsetParams mp = {};
+        mp.dst = L.ctl;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 4;  // ctl[0 .. 1]
+        mp.height = 1;
+        cudaGraphNode_t zero;
+        if ((e = cudaGraphAddMemsetNode(&zero, G.g, nullptr, 0, &mp)) != cudaSuccess) { fail(e, "graph memset"); break; }
+        cudaGraphNodeParams wp = {};
+        wp.type = cudaGraphNodeTypeConditional;
+        wp.conditional.handle = hw;
+        wp.conditional.type = cudaGraphCondTypeWhile;
+        wp.conditional.size = 1;
+        cudaGraphNode_t wn;
+        if ((e = cudaGraphAddNode(&wn, G.g, &zero, nullptr, 1, &wp)) != cudaSuccess) { fail(e, "graph while"); break; }
+        cudaGraph_t body = wp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(cb, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+            cudaSuccess) {
+            fail(e, "graph capture");
+            break;
+        }
+        long long k0 = thread_launch_count();
+        launch_compact_active(L.active, L.S, L.cols, L.cnt, cb);
+        launch_lanc_ctrl(L.cnt, L.counters, L.S, h->dev_err, guard, L.ctl, L.stat, hw, hf, hs, 1, cb);
+        G.k_iter = thread_launch_count() - k0;
+        cudaGraph_t bf = nullptr, bs = nullptr;
+        e = capture_conditional(cb, hf, cudaGraphCondTypeIf, &bf);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cf, bf, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            k0 = thread_launch_count();
+            const int r = finish_batch(h, o, L, neps, sig_all, res_all, flags_all, member_all, cf);
+            G.k_fin = thread_launch_count() - k0;
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cf, &out);
+            if (r < 0) rc = r;
+            e = e2;
+        }
+        if (e == cudaSuccess && !rc) e = capture_conditional(cb, hs, cudaGraphCondTypeIf, &bs);
+        if (e == cudaSuccess && !rc)
+            e = cudaStreamBeginCaptureToGraph(cf, bs, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess && !rc) {
+            k0 = thread_launch_count();
+            const cudaError_t e1 = lanczos_step(h, L, a, L.S, cf, true);
+            G.k_step = thread_launch_count() - k0;
+            cudaGraph_t out = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(cf, &out);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+        cudaGraph_t outb = nullptr;
+        const cudaError_t e3 = cudaStreamEndCapture(cb, &outb);
+        if (e == cudaSuccess) e = e3;
+        if (e != cudaSuccess) { fail(e, "graph capture"); break; }
+        if (rc) break;
+        if ((e = cudaGraphInstantiate(&G.x, G.g, 0)) != cudaSuccess) { fail(e, "graph instantiate"); break; }
+    } while (false);
+    cudaStreamDestroy(cb);
+    cudaStreamDestroy(cf);
+    return rc;
+}
+
 // Continuous-batching Lanczos over the npts points zall (device) with the
-// outputs in the same order; eps levels must already be in L.eps.
+// outputs in the same order; eps levels must already be in L.eps.  The loop
+// runs on the device (build_lanc_graph) unless kernel profiling or
+// opts.device_loop = 0 asks for the host-driven loop, which reads the slot
+// counts back after every step.
 static int run_points(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, const double2 *zall, int64_t npts, int neps,
                       double *sig_all, double *res_all, int32_t *flags_all, uint32_t *member_all, cudaStream_t s,
                       const double2 *vw = nullptr, int64_t ldw = 0, const int *posw = nullptr, int offw = 0) {
-    const int n = h->n, S = L.S;
-    const int64_t qs = (int64_t)n * S;
+    const int S = L.S;
     cudaError_t e;
     cudaMemsetAsync(L.nbad, 0, sizeof(int), s);
     cudaMemsetAsync(L.counters, 0, 4 * sizeof(int), s);
+    cudaMemsetAsync(L.stat, 0, 8 * sizeof(long long), s);
+    if (L.Rz) cudaMemsetAsync(L.Rz, 0xff, S * sizeof(double2), s);  // NaN: no slot holds a factor yet
     if (L.fb_cnt) cudaMemsetAsync(L.fb_cnt, 0, sizeof(int), s);
-    launch_start_vector(L.startv, n, o->seed, s);
+    launch_start_vector(L.startv, h->n, o->seed, s);
 
     const double rt = o->rtol > 0.0 ? o->rtol : 1e-8;
+    StepArgs a;
+    memset(&a, 0, sizeof a);  // its bytes (padding included) key the graph cache
+    a.zall = zall;
+    a.npts = npts;
+    a.vw = vw;
+    a.ldw = ldw;
+    a.posw = posw;
+    a.offw = offw;
     // mixed precision: the Ritz vector only starts the refinement step, whose
     // Rayleigh quotient error is the square of the vector error after one
     // inverse-iteration step, so 1e-9 on the Ritz value is ample for 1e-8 on sigma
-    const double tol_q = L.fp32 ? 1e-9 : rt / 2.0;
-    const double tol_floor = L.fp32 ? 1e-6 : 1e-15;
-    const int passes = L.fp32 ? 1 : 2;  // Gram-Schmidt passes of the reorthogonalisation
+    a.tol_q = L.fp32 ? 1e-9 : rt / 2.0;
+    a.tol_floor = L.fp32 ? 1e-6 : 1e-15;
+    a.passes = L.fp32 ? 1 : 2;  // Gram-Schmidt passes of the reorthogonalisation
 
     // fill every slot with a point
     launch_fill_int(L.active, S, 3, s);
-    auto harvest = [&]() {
+    {
+        const int64_t qs = (int64_t)h->n * S;
         if (L.fp32)
-            launch_slot_harvest<float>((float2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd, L.pt,
-                                       L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
+            launch_slot_harvest<float>((float2 *)L.Q, qs, h->n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd,
+                                       L.pt, L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
                                        L.fin_theta, L.fin_conv, L.startv, L.hwork, s);
         else
-            launch_slot_harvest<double>((double2 *)L.Q, qs, n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd,
+            launch_slot_harvest<double>((double2 *)L.Q, qs, h->n, S, L.mmax, L.svec, L.jv, L.active, L.theta, L.convd,
                                         L.pt, L.zslot, zall, (int)npts, L.counters, L.Ufin, L.F, L.fin_pt, L.fin_z,
                                         L.fin_theta, L.fin_conv, L.startv, L.hwork, s, vw, ldw, posw, offw);
-    };
-    harvest();
+    }
+    // every point takes at most mmax steps and every finish empties the
+    // buffer: a bound on the iterations of the whole loop
+    const long long bound = 4 * ((npts + S - 1) / S + 2) * (long long)(L.mmax + 2) + 64;
     int host[4];
-    for (int iter = 0;; ++iter) {
+    bool done = false;
+    if (o->device_loop && !h->prof) {
+        std::vector<unsigned char> key;
+        key_put(key, L);
+        key_put(key, a);
+        key_put(key, neps);
+        key_put(key, sig_all);
+        key_put(key, res_all);
+        key_put(key, flags_all);
+        key_put(key, member_all);
+        key_put(key, bound);
+        key_put(key, o->max_ir);
+        key_put(key, h->fp32_solver);
+        key_put(key, h->wait_ns);
+        if (!h->graph_cache) h->graph_cache = new GraphCache();
+        GraphCache &gc = *h->graph_cache;
+        LancGraph *gp = nullptr;
+        for (auto &x : gc.e)
+            if (x.key == key) {
+                gp = x.g;
+                x.used = ++gc.tick;
+            }
+        if (!gp) {
+            const auto tb = std::chrono::steady_clock::now();
+            gp = new LancGraph();
+            const int rc = build_lanc_graph(h, o, L, a, neps, sig_all, res_all, flags_all, member_all, bound, *gp);
+            if (rc < 0) {
+                delete gp;
+                return rc;
+            }
+            if ((int)gc.e.size() >= GRAPH_CACHE) {
+                auto lru = std::min_element(gc.e.begin(), gc.e.end(),
+                                            [](const GraphCache::Entry &x, const GraphCache::Entry &y) {
+                                                return x.used < y.used;
+                                            });
+                delete lru->g;
+                gc.e.erase(lru);
+            }
+            gc.e.push_back({key, gp, ++gc.tick});
+            h->stats.n_graph_builds += 1;
+            h->stats.ms_graph_build +=
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tb).count();
+        }
+        LancGraph &G = *gp;
+        long long iters = 0, ctl[2] = {0, 0}, st0[4], st1[4];
+        cudaMemcpyAsync(st0, L.stat, sizeof(st0), cudaMemcpyDeviceToHost, s);
+        for (;;) {
+            if ((e = cudaGraphLaunch(G.x, s)) != cudaSuccess) return cuda_err(e, "graph launch");
+            h->stats.n_graph_launches += 1;
+            cudaMemcpyAsync(ctl, L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&host[0], L.cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&host[1], L.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(&host[3], h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "lanczos");
+            iters += ctl[0];
+            if (host[3]) break;                      // a bounded wait gave up: reported by the caller
+            if (host[0] == 0 && host[2] == 0) break;  // no running slot, nothing left to finish
+            if (iters > bound) return set_err(PSEUDO_ERR_TIMEOUT, "Lanczos driver did not terminate");
+        }
+        cudaMemcpyAsync(st1, L.stat, sizeof(st1), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "lanczos");
+        note_launches(iters * G.k_iter + (st1[3] - st0[3]) * G.k_fin + (st1[0] - st0[0]) * G.k_step);
+        done = true;
+    }
+    for (long long iter = 0; !done; ++iter) {
         launch_compact_active(L.active, S, L.cols, L.cnt, s);
+        launch_lanc_ctrl(L.cnt, L.counters, S, h->dev_err, 0, L.ctl, L.stat, 0, 0, 0, 0, s);
         cudaMemcpyAsync(&host[0], L.cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&host[1], L.counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&host[3], h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "lanczos");
+        if (host[3]) break;
         const int ncnt = host[0], nfin = host[2];
         if (nfin >= S || (ncnt == 0 && nfin > 0)) {
-            const int rc = finish_batch(h, o, L, nfin, neps, sig_all, res_all, flags_all, member_all, s);
+            const int rc = finish_batch(h, o, L, neps, sig_all, res_all, flags_all, member_all, s);
             if (rc < 0) return rc;
-            cudaMemsetAsync(L.counters + 1, 0, sizeof(int), s);
         }
         if (ncnt == 0) break;
-        if (L.fp32) {
-            float2 *Q = (float2 *)L.Q, *W = (float2 *)L.W;
-            launch_slot_copy<float>(Q, qs, W, n, S, L.jv, L.active, s);
-            int k0 = kp_begin(h, s);
-            e = solve32(h, 1, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
-            kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
-            k0 = kp_begin(h, s);
-            if (e == cudaSuccess)
-                e = solve32(h, 0, L.cols, L.zslot, ncnt, L.cnt, W, S, (float2 *)L.xs, s);
-            kp_end(h, k0, PSEUDO_K_TRSV32, tri_flops(n, ncnt), tri_bytes(n, ncnt, 8, 8, 2), s);
-            k0 = kp_begin(h, s);
-            launch_slot_orth_grid<float>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, L.Hp, L.nrm2,
-                                         L.alpha_acc, s);
-            kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
-        } else {
-            double2 *Q = (double2 *)L.Q, *W = (double2 *)L.W;
-            launch_slot_copy<double>(Q, qs, W, n, S, L.jv, L.active, s);
-            e = cudaSuccess;
-            for (int lower = 1; lower >= 0 && e == cudaSuccess; --lower) {
-                const int k0 = kp_begin(h, s);
-                e = launch_trsv64(lower ? h->L64 : h->U64, n, h->n_pad, lower, L.cols, L.zslot, ncnt, L.cnt, W, S,
-                                  (double2 *)L.xs, s);
-                kp_end(h, k0, PSEUDO_K_TRSV64, tri_flops(n, ncnt), tri_bytes(n, ncnt, 16, 16, 2), s);
-            }
-            const int k0 = kp_begin(h, s);
-            launch_slot_orth_grid<double>(Q, qs, W, n, S, L.jv, L.mmax, L.active, L.alpha, L.beta, passes, L.Hp, L.nrm2,
-                                          L.alpha_acc, s);
-            kp_end(h, k0, PSEUDO_K_LANCZOS, 0.0, 0.0, s);
-        }
-        if (e != cudaSuccess) return cuda_err(e, "lanczos solve");
-        h->stats.sv_R += 2 * (int64_t)ncnt;
-        h->stats.lanczos_steps += 1;
-        launch_slot_tridiag(S, L.mmax, L.alpha, L.beta, L.active, L.jv, L.theta, L.svec, L.convd, tol_q, tol_floor,
-                            L.fp32 ? 1 : 0, s);
-        harvest();
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "lanczos step");
+        if (iter > bound) return set_err(PSEUDO_ERR_TIMEOUT, "Lanczos driver did not terminate");
+        if ((e = lanczos_step(h, L, a, ncnt, s)) != cudaSuccess) return cuda_err(e, "lanczos step");
     }
+    long long st[4];
+    cudaMemcpyAsync(st, L.stat, sizeof(st), cudaMemcpyDeviceToHost, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "lanczos");
+    h->stats.lanczos_steps += st[0];
+    h->stats.sv_R += st[1];
+    h->stats.mv_M_fp64_refine += st[2];
     return 0;
+}
+
+void graph_cache_free(pseudo_ctx *h) {
+    delete h->graph_cache;
+    h->graph_cache = nullptr;
 }
 
 int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s) {

@@ -620,7 +620,7 @@ slot_refill_kernel(cx_t<real> *__restrict__ Q, int n, int S, const int4 *__restr
 
 // Results of finished points t < P (sigma from theta or from the Rayleigh
 // quotient s2), scattered to their grid positions.
-__global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const double2 *__restrict__ fin_z,
+__global__ void fin_scatter_kernel(int P_host, const int *__restrict__ P_dev, const int *__restrict__ fin_pt, const double2 *__restrict__ fin_z,
                                    const double *__restrict__ fin_theta, const int *__restrict__ fin_conv,
                                    const double *__restrict__ s2, const double *__restrict__ rr, int use_rq,
                                    double norm2, const double *__restrict__ eps, int neps, double *__restrict__ sigma_out,
@@ -630,6 +630,7 @@ __global__ void fin_scatter_kernel(int P, const int *__restrict__ fin_pt, const 
                                    const double2 *__restrict__ U0, int64_t ldu, double2 *__restrict__ warm,
                                    int64_t ldw, int n, const double2 *__restrict__ v0) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = P_dev ? min(*P_dev, P_host) : P_host;
     if (t >= P) return;
     const double th = fin_theta[t];
     const double rq = sqrt(fmax(s2[t], 0.0));
@@ -710,13 +711,56 @@ void launch_fin_scatter(int P, const int *fin_pt, const double2 *fin_z, const do
                         const double *s2, const double *rr, int use_rq, double norm2, const double *eps, int neps,
                         double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out, int *nbad,
                         double u_solve, double fb_ku, int *fb_list, int *fb_cnt, cudaStream_t s, const double2 *U0,
-                        int64_t ldu, double2 *warm, int64_t ldw, int n, const double2 *v0) {
+                        int64_t ldu, double2 *warm, int64_t ldw, int n, const double2 *v0, const int *P_dev) {
     if (P > 0) {
-        note_launch(); fin_scatter_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, fin_pt, fin_z, fin_theta, fin_conv, s2, rr, use_rq, norm2,
+        note_launch(); fin_scatter_kernel<<<(P + 127) / 128, 128, 0, s>>>(P, P_dev, fin_pt, fin_z, fin_theta, fin_conv, s2, rr, use_rq, norm2,
                                                                         eps, neps, sigma_out, res_out, flags_out,
                                                                         member_out, nbad, u_solve, fb_ku, fb_list,
                                                                         fb_cnt, U0, ldu, warm, ldw, n, v0);
     }
+}
+
+// mask[c] = 1 for c < *P, 0 for the other columns up to F
+__global__ void mask_prefix_kernel(int *__restrict__ mask, int F, const int *__restrict__ P) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < F) mask[c] = c < *P ? 1 : 0;
+}
+void launch_mask_prefix(int *mask, int F, const int *P, cudaStream_t s) {
+    if (F > 0) { note_launch(); mask_prefix_kernel<<<(F + 255) / 256, 256, 0, s>>>(mask, F, P); }
+}
+
+// Loop control of the device-driven Lanczos driver (one thread), after the
+// compaction of the running slots: finish the finished buffer when it holds
+// S points or when no slot runs and it is not empty; step while a slot runs.
+// The loop stops early after `guard` iterations of one launch, or when a
+// bounded wait of a tensor-core kernel gave up (err[0]); the host then
+// resumes or reports.  ctl[0] counts this launch's iterations (zeroed by the
+// launch), stat[0] the steps, stat[1] the solves (2 per running slot and
+// step), stat[2] the Rayleigh-quotient products of the finishes (2 per
+// point), stat[3] the finishes.  With graph = 0 it only counts.
+__global__ void lanc_ctrl_kernel(const int *__restrict__ cnt, const int *__restrict__ counters, int S,
+                                 const int *__restrict__ err, long long guard, long long *__restrict__ ctl,
+                                 long long *__restrict__ stat, cudaGraphConditionalHandle hw,
+                                 cudaGraphConditionalHandle hf, cudaGraphConditionalHandle hs, int graph) {
+    if (threadIdx.x | blockIdx.x) return;
+    const int c = *cnt, nfin = counters[1];
+    const long long it = ++ctl[0];
+    const bool fin = nfin >= S || (c == 0 && nfin > 0);
+    const bool ok = err[0] == 0;
+    const bool step = c > 0 && ok;
+    if (fin && ok) { stat[2] += 2 * (long long)nfin; stat[3] += 1; }
+    if (step) { stat[0] += 1; stat[1] += 2 * (long long)c; }
+    if (graph) {
+        cudaGraphSetConditional(hf, fin && ok ? 1u : 0u);
+        cudaGraphSetConditional(hs, step ? 1u : 0u);
+        cudaGraphSetConditional(hw, step && it < guard ? 1u : 0u);
+    }
+}
+void launch_lanc_ctrl(const int *cnt, const int *counters, int S, const int *err, long long guard, long long *ctl,
+                      long long *stat, cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hf,
+                      cudaGraphConditionalHandle hs, int graph, cudaStream_t s) {
+    note_launch();
+    lanc_ctrl_kernel<<<1, 32, 0, s>>>(cnt, counters, S, err, guard, ctl, stat, hw, hf, hs, graph);
 }
 
 __global__ void fb_gather_kernel(const int *__restrict__ list, int cnt, const double2 *__restrict__ zall,

@@ -19,7 +19,13 @@
 namespace pseudo {
 
 static std::atomic<long long> g_launches{0};
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void note_launch() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long thread_launch_count() { return t_launches; }
 
 static thread_local std::string g_err;
 
@@ -74,6 +80,7 @@ int pseudo_opts_default(pseudo_opts *o) {
     o->max_ir = 6;
     o->seed = 12345;
     o->fp32_solver = PSEUDO_SOLVER_AUTO;
+    o->device_loop = 1;
     return PSEUDO_OK;
 }
 
@@ -83,21 +90,28 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if (!out) return set_err(PSEUDO_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!T) return set_err(PSEUDO_ERR_ARG, "T is NULL");
-    if (m != n) return set_err(PSEUDO_ERR_UNSUPPORTED, "rectangular input (m=%lld, n=%lld) is not supported", (long long)m, (long long)n);
     if (n < 1 || n > (1 << 20)) return set_err(PSEUDO_ERR_ARG, "n=%lld out of range", (long long)n);
-    if (ldT < n) return set_err(PSEUDO_ERR_ARG, "ldT=%lld < n=%lld", (long long)ldT, (long long)n);
+    if (m != n && m != 2 * n)
+        return set_err(PSEUDO_ERR_UNSUPPORTED, "m=%lld rows: the input is T (m = n) or the pencil [T; B] (m = 2n = %lld)",
+                       (long long)m, 2 * (long long)n);
+    if (ldT < m) return set_err(PSEUDO_ERR_ARG, "ldT=%lld < m=%lld", (long long)ldT, (long long)m);
+    if (m == 2 * n && n > rect_max_order())
+        return set_err(PSEUDO_ERR_UNSUPPORTED, "a rectangular pencil needs n <= %d", rect_max_order());
     cudaStream_t s = (cudaStream_t)stream;
     pseudo_ctx *h = new pseudo_ctx();
     h->n = (int)n;
+    h->rect = m == 2 * n;
     h->n_pad = (int)((n + TC_MB - 1) / TC_MB * TC_MB);  // a multiple of both panel heights
     cudaGetDevice(&h->dev);
     const int64_t psz = packed_size(h->n_pad);
     cudaError_t e;
     double2 *Td = nullptr;
+    float2 *b32 = nullptr;
     int *bad = nullptr;
     double *dsum = nullptr;
     auto fail = [&](int code) {
         if (Td && t_on_host) cudaFree(Td);
+        if (b32) cudaFree(b32);
         if (bad) cudaFree(bad);
         if (dsum) cudaFree(dsum);
         pseudo_destroy(h);
@@ -130,46 +144,81 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
         Td = (double2 *)T;
     }
     launch_pack_panels(Td, ldT, (int)n, h->n_pad, h->U64, h->L64, h->U32, h->L32, s);
+    if (h->rect) {
+        // the bottom block B (rows n .. 2n-1): FP64 panels of B and B^H (its FP32
+        // panels are not kept), and the dense pencil for the per-point QR
+        if ((e = cudaMalloc(&h->BU64, psz * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc BU64"));
+        if ((e = cudaMalloc(&h->BL64, psz * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc BL64"));
+        if ((e = cudaMalloc(&b32, 2 * psz * sizeof(float2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
+        if ((e = cudaMalloc(&h->M64, 2 * (size_t)n * n * sizeof(double2))) != cudaSuccess)
+            return fail(cuda_err(e, "cudaMalloc M64"));
+        launch_pack_panels(Td + n, ldT, (int)n, h->n_pad, h->BU64, h->BL64, b32, b32 + psz, s);
+        if ((e = cudaMemcpy2DAsync(h->M64, 2 * n * sizeof(double2), Td, ldT * sizeof(double2), 2 * n * sizeof(double2),
+                                   n, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return fail(cuda_err(e, "copy M"));
+    }
     launch_pack_tc(Td, ldT, (int)n, h->n_pad, h->tcA_U, h->tcA_L, h->tcD_U, h->tcD_L, s);
     launch_pack_oz(Td, ldT, (int)n, h->n_pad, h->ozA_U, h->ozA_L, h->ozE_U, h->ozE_L, s);
     launch_pack_lo(h->U64, h->U32, h->U32lo, psz, s);
     launch_pack_lo(h->L64, h->L32, h->L32lo, psz, s);
     cudaMemsetAsync(bad, 0, sizeof(int), s);
     launch_nonfinite(h->U64, psz, bad, s);
+    if (h->rect) launch_nonfinite(h->BU64, psz, bad, s);
     launch_extract_diag(h->U64, (int)n, h->n_pad, h->diag, s);
     launch_sumsq(h->U64, psz, dsum, s);
     int hbad = 0;
-    double fro2 = 0.0;
+    double fro2 = 0.0, fro2b = 0.0;
     cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(&fro2, dsum, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (h->rect) {
+        launch_sumsq(h->BU64, psz, dsum + 1, s);
+        cudaMemcpyAsync(&fro2b, dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_err(e, "pack T"));
-    if (hbad) return fail(set_err(PSEUDO_ERR_NONFINITE, "T has non-finite entries in its upper triangle"));
-    h->norm_fro = sqrt(fro2);
-    // ||T||_2 estimate: power iteration on T^H T from a seeded vector
+    if (hbad) return fail(set_err(PSEUDO_ERR_NONFINITE, "T (or B) has non-finite entries in its upper triangle"));
+    h->norm_fro = sqrt(fro2 + fro2b);
+    // ||M||_2 estimate (M = T, or [T; B]): power iteration on M^H M from a seeded vector
     {
         double2 *x = nullptr, *y = nullptr;
         if ((e = cudaMalloc(&x, n * sizeof(double2))) != cudaSuccess) return fail(cuda_err(e, "cudaMalloc"));
         if ((e = cudaMalloc(&y, n * sizeof(double2))) != cudaSuccess) { cudaFree(x); return fail(cuda_err(e, "cudaMalloc")); }
         launch_start_vector(x, (int)n, 99, s);
         double lam = 0.0;
+        double2 *yb = nullptr;
+        if (h->rect && (e = cudaMalloc(&yb, 2 * n * sizeof(double2))) != cudaSuccess) {
+            cudaFree(x);
+            cudaFree(y);
+            return fail(cuda_err(e, "cudaMalloc"));
+        }
         for (int it = 0; it < 30; ++it) {
+            // rectangular: x <- T^H T x + B^H B x (the current x is kept in yb)
+            if (h->rect) cudaMemcpyAsync(yb, x, n * sizeof(double2), cudaMemcpyDeviceToDevice, s);
             launch_trmv64(h->U64, (int)n, h->n_pad, 0, nullptr, nullptr, 1, nullptr, x, 1, nullptr, 1, y, 1, 0, s);
             launch_trmv64(h->L64, (int)n, h->n_pad, 1, nullptr, nullptr, 1, nullptr, y, 1, nullptr, 1, x, 1, 0, s);
+            if (h->rect) {
+                launch_trmv64(h->BU64, (int)n, h->n_pad, 0, nullptr, nullptr, 1, nullptr, yb, 1, nullptr, 1, y, 1, 0, s);
+                launch_trmv64(h->BL64, (int)n, h->n_pad, 1, nullptr, nullptr, 1, nullptr, y, 1, nullptr, 1, yb + n, 1, 0,
+                              s);
+                launch_add_cols(x, yb + n, n, s);
+            }
             launch_colnorm2(x, (int)n, 1, nullptr, dsum, s);
             double nx2 = 0.0;
             cudaMemcpyAsync(&nx2, dsum, sizeof(double), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
-            lam = sqrt(nx2);  // ||T^H T x|| for unit x
+            lam = sqrt(nx2);  // ||M^H M x|| for unit x
             if (!(lam > 0.0)) break;
             launch_normalize(x, (int)n, 1, nullptr, s);
         }
         cudaFree(x);
         cudaFree(y);
+        if (yb) cudaFree(yb);
         h->norm2 = lam > 0.0 ? sqrt(lam) : h->norm_fro;
         if (h->norm2 > h->norm_fro) h->norm2 = h->norm_fro;
     }
     if (t_on_host) cudaFree(Td);
     Td = nullptr;
+    if (b32) cudaFree(b32);
+    b32 = nullptr;
     cudaFree(bad); bad = nullptr;
     cudaFree(dsum); dsum = nullptr;
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(cuda_err(e, "create"));
@@ -195,6 +244,10 @@ int pseudo_set_wait_limit(pseudo_handle h, uint64_t ns) {
 
 void pseudo_destroy(pseudo_handle h) {
     if (!h) return;
+    graph_cache_free(h);
+    cudaFree(h->M64);
+    cudaFree(h->BU64);
+    cudaFree(h->BL64);
     cudaFree(h->U64);
     cudaFree(h->L64);
     cudaFree(h->U32);
@@ -270,6 +323,7 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
                  void *workspace, size_t workspace_bytes, void *stream) {
     clear_err();
     if (!h || !X || !z || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "shifted solves need a square handle (m = n)");
     if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE &&
         precision != PSEUDO_DOUBLE_SINGLE)
         return set_err(PSEUDO_ERR_ARG, "bad precision");
@@ -318,6 +372,7 @@ int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pse
                   void *stream) {
     clear_err();
     if (!h || !X || !Y || ncols < 0 || (subtract && !B)) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "products with T - zI need a square handle (m = n)");
     if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE)
         return set_err(PSEUDO_ERR_ARG, "bad precision");
     if (ncols > (1 << 18)) return set_err(PSEUDO_ERR_ARG, "ncols too large");
@@ -351,6 +406,7 @@ static int check_opts(const pseudo_opts *o) {
     if (o->max_ir < 1 || o->max_ir > 32) return set_err(PSEUDO_ERR_ARG, "max_ir must be in [1, 32]");
     if (o->shift_batch < 0) return set_err(PSEUDO_ERR_ARG, "shift_batch < 0");
     if (o->fp32_solver < 0 || o->fp32_solver > PSEUDO_SOLVER_AUTO) return set_err(PSEUDO_ERR_ARG, "bad fp32_solver");
+    if (o->device_loop != 0 && o->device_loop != 1) return set_err(PSEUDO_ERR_ARG, "device_loop must be 0 or 1");
     if (!(o->rtol >= 0.0)) return set_err(PSEUDO_ERR_ARG, "rtol < 0");
     if (o->mode == PSEUDO_RECYCLE) {
         if (o->r < 1 || o->r > 8) return set_err(PSEUDO_ERR_ARG, "r must be in [1, 8]");
@@ -364,10 +420,18 @@ static int check_opts(const pseudo_opts *o) {
     return PSEUDO_OK;
 }
 
+// The rectangular pencil (m = 2n) runs FP64 inverse Lanczos only.
+static int check_rect(const pseudo_ctx *h, const pseudo_opts *o) {
+    if (h->rect && (o->mode != PSEUDO_INVLANC || o->precision != PSEUDO_FP64))
+        return set_err(PSEUDO_ERR_UNSUPPORTED, "a rectangular pencil (m = 2n) runs mode INVLANC in precision FP64 only");
+    return PSEUDO_OK;
+}
+
 int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, size_t *bytes) {
     clear_err();
     if (!h || !bytes || npts < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
     int rc = check_opts(o);
+    if (!rc) rc = check_rect(h, o);
     if (rc) return rc;
     Carver c;
     if (o->mode == PSEUDO_INVLANC) invlanc_carve(h, o, npts, c, nullptr);
@@ -380,7 +444,8 @@ int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t n
     clear_err();
     if (!h || !o || !out || npts < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (o->mode != PSEUDO_RECYCLE) return set_err(PSEUDO_ERR_ARG, "recycle mode only");
-    const int rc = check_opts(o);
+    int rc = check_opts(o);
+    if (!rc) rc = check_rect(h, o);
     if (rc) return rc;
     recycle_state_layout(h, o, npts, out);
     return PSEUDO_OK;
@@ -392,6 +457,7 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
     clear_err();
     if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
     int rc = check_opts(o);
+    if (!rc) rc = check_rect(h, o);
     if (rc) return rc;
     if (npts < 0 || npts >= (int64_t)1 << 31) return set_err(PSEUDO_ERR_ARG, "npts out of range");
     if (npts == 0) return PSEUDO_OK;

@@ -53,6 +53,7 @@ extern "C" int pseudo_solve_noalloc(pseudo_handle h, pseudo_c64 *X, const pseudo
                                     void *stream) {
     clear_err();
     if (!h || !X || !z || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "shifted solves need a square handle (m = n)");
     if (ncols == 0) return PSEUDO_OK;
     // Each group of 8 columns needs at least 128 scratch elements, so more
     // than NOALLOC_SCRATCH_ELEMS columns can never fit; rejecting them here

@@ -18,6 +18,8 @@
 // with warp shuffles.  Solutions already computed are read from a compact
 // per-CTA copy (scratch: 64-row-padded n x R per CTA), so every x_k load is a
 // contiguous broadcast of R values.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -60,7 +62,8 @@ template <typename real, int R, int NW>
 __global__ void __launch_bounds__(NW * 32)
 trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
-               const int *__restrict__ ncols_dev, cx_t<real> *X, int64_t ldx, cx_t<real> *xs_all) {
+               const int *__restrict__ ncols_dev, cx_t<real> *X, int64_t ldx, cx_t<real> *xs_all, int cmin,
+               int cmax) {
     using C = cx_t<real>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *red = reinterpret_cast<C *>(smem_raw);   // [NW][PH][R]
@@ -70,7 +73,9 @@ trsv_ms_kernel(const cx_t<real> *__restrict__ Pn, int n, int n_pad, int lower,
 
     const int ncols = ncols_dev ? *ncols_dev : ncols_host;
     const int g = blockIdx.x;
-    if (g * R >= ncols) return;
+    // [cmin, cmax]: the live counts this column-group width serves (one of
+    // several launches over an upper bound of the count; the others leave)
+    if (g * R >= ncols || ncols < cmin || ncols > cmax) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x < R) {
         int pos = g * R + threadIdx.x;
@@ -220,13 +225,15 @@ static size_t trsv_smem() { return sizeof(cx_t<real>) * (size_t)(NW * PH * R + P
 template <typename real, int R, int NW>
 static cudaError_t trsv_launch(const cx_t<real> *Pn, int n, int n_pad, int lower, const int *cols,
                                const double2 *zc, int ncols, const int *ncols_dev, cx_t<real> *X,
-                               int64_t ldx, cx_t<real> *xs, cudaStream_t s) {
+                               int64_t ldx, cx_t<real> *xs, cudaStream_t s, int cmin = 0,
+                               int cmax = 0x7fffffff) {
     size_t sm = trsv_smem<real, R, NW>();
     static std::atomic<uint64_t> attr{0};
     smem_attr_once(trsv_ms_kernel<real, R, NW>, (int)sm, attr);
     int grid = (ncols + R - 1) / R;
     if (grid == 0) return cudaSuccess;
-    note_launch(); trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs);
+    note_launch(); trsv_ms_kernel<real, R, NW><<<grid, NW * 32, sm, s>>>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs,
+                                                                  cmin, cmax);
     return cudaGetLastError();
 }
 
@@ -250,6 +257,20 @@ cudaError_t launch_trsv64(const double2 *Pn, int n, int n_pad, int lower, const 
     if (ncols <= 1184)
         return trsv_launch<double, 2, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return trsv_launch<double, R64, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+}
+cudaError_t launch_trsv64_bounded(const double2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
+                                  int bound, const int *ncols_dev, double2 *X, int64_t ldx, double2 *xs,
+                                  cudaStream_t s) {
+    // the live count is known only on the device: one launch per column-group
+    // width that a count up to `bound` may need, each serving its own range
+    cudaError_t e = trsv_launch<double, 1, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, std::min(bound, 296), ncols_dev, X,
+                                                     ldx, xs, s, 0, 296);
+    if (e == cudaSuccess && bound > 296)
+        e = trsv_launch<double, 2, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, std::min(bound, 1184), ncols_dev, X, ldx,
+                                             xs, s, 297, 1184);
+    if (e == cudaSuccess && bound > 1184)
+        e = trsv_launch<double, R64, NW_SOLVE>(Pn, n, n_pad, lower, cols, zc, bound, ncols_dev, X, ldx, xs, s, 1185);
+    return e;
 }
 cudaError_t launch_trsv32(const float2 *Pn, int n, int n_pad, int lower, const int *cols, const double2 *zc,
                           int ncols, const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {

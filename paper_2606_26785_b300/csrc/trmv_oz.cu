@@ -179,10 +179,11 @@ void launch_pack_oz(const double2 *T, int64_t ldT, int n, int n_pad, void *AUv, 
 // ------------------------------------------------------------ X slicing
 // f_p for listed column p: max_k |Re|, |Im| of column cols[p] < 2^f_p
 __global__ void oz_colexp_kernel(const double2 *__restrict__ X, int n, int64_t ldx, const int *__restrict__ cols,
-                                 int ncols, int *__restrict__ fx) {
+                                 int ncols, const int *__restrict__ ncols_dev, int *__restrict__ fx) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int p = blockIdx.x * 32 + lane;
-    const int c = p < ncols ? (cols ? cols[p] : p) : -1;
+    const int nl = ncols_dev ? min(*ncols_dev, ncols) : ncols;  // live columns
+    const int c = p < nl ? (cols ? cols[p] : p) : -1;
     double m = 0.0;
     if (c >= 0)
         for (int i = warp; i < n; i += nw) {
@@ -204,10 +205,11 @@ __global__ void oz_colexp_kernel(const double2 *__restrict__ X, int n, int64_t l
 // real K entries), so that every slice is written as one 16-byte core-matrix
 // row (8 consecutive bf16) and a warp reads 32 consecutive columns of X.
 __global__ void oz_slice_b_kernel(const double2 *__restrict__ X, int n, int n_pad, int64_t ldx,
-                                  const int *__restrict__ cols, int ncols, const int *__restrict__ fx,
-                                  __nv_bfloat16 *__restrict__ img) {
+                                  const int *__restrict__ cols, int ncols, const int *__restrict__ ncols_dev,
+                                  const int *__restrict__ fx, __nv_bfloat16 *__restrict__ img) {
     const int64_t NCH = nchunks(n_pad);
-    const int64_t tiles = (ncols + OZ_NC - 1) / OZ_NC;
+    const int nl = ncols_dev ? min(*ncols_dev, ncols) : ncols;  // live columns; the layout follows ncols
+    const int64_t tiles = (nl + OZ_NC - 1) / OZ_NC;
     constexpr int KG = OZ_KR / 8;  // groups of 8 real K entries: real parts first, then imaginary parts
     const int64_t total = tiles * NCH * OZ_NC * KG;
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
@@ -217,7 +219,7 @@ __global__ void oz_slice_b_kernel(const double2 *__restrict__ X, int n, int n_pa
         const int64_t ct = tc_ / NCH, ch = tc_ % NCH;
         const int p = (int)(ct * OZ_NC + j);
         const int part = kg / (KG / 2), kb = (kg % (KG / 2)) * 8;
-        const bool live = p < ncols;
+        const bool live = p < nl;
         const int c = live ? (cols ? cols[p] : p) : 0;
         const int f = live ? fx[p] : 0;
         float a[8][OZ_NS];
@@ -274,9 +276,9 @@ struct OzSmem {
 __global__ void __launch_bounds__(OZ_TH, 1)
 trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ ex, const __nv_bfloat16 *__restrict__ Bimg,
                const int *__restrict__ fx, int n, int n_pad, int lower, const int *__restrict__ cols,
-               const double2 *__restrict__ zc, int ncols, const double2 *__restrict__ X, int64_t ldx,
-               const double2 *__restrict__ B, int64_t ldb, double2 *__restrict__ Y, int64_t ldy, int subtract,
-               int *err, uint64_t wait_ns) {
+               const double2 *__restrict__ zc, int ncols, const int *__restrict__ ncols_dev,
+               const double2 *__restrict__ X, int64_t ldx, const double2 *__restrict__ B, int64_t ldb,
+               double2 *__restrict__ Y, int64_t ldy, int subtract, int *err, uint64_t wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_ld[OZ_NSTG], bar_mma[OZ_NSTG];
     __shared__ uint32_t s_tmem;
@@ -295,6 +297,10 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
     const int64_t w_in = lin - grp * OZ_GR * tiles;
     const int iy = (int)grp * OZ_GR + (int)(w_in % rows_in);
     const int ct = (int)(w_in / rows_in);
+    // with a device column count the grid covers ncols (an upper bound) and
+    // the tiles past the live columns leave at once
+    const int nl = ncols_dev ? min(*ncols_dev, ncols) : ncols;
+    if (ct * OZ_NC >= nl) return;
     const int I = lower ? NT - 1 - iy : iy;
     int c0, c1;
     chunk_range(I, n_pad, lower, c0, c1);
@@ -416,7 +422,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
         const int part = rr / OZ_CR, i = I * OZ_CR + (rr % OZ_CR);
         if (i < n) {
             const int e_i = ex[i];
-            const int jmax = min(HC, ncols - ct * OZ_NC - hc * HC);
+            const int jmax = min(HC, nl - ct * OZ_NC - hc * HC);
             for (int jj = 0; jj < jmax; ++jj) {
                 const int j = hc * HC + jj;
                 const int p = ct * OZ_NC + j;
@@ -451,7 +457,7 @@ trmv_oz_kernel(const __nv_bfloat16 *__restrict__ Apack, const int *__restrict__ 
 
 cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const double2 *X, int64_t ldx, const double2 *B, int64_t ldb, double2 *Y, int64_t ldy,
-                           int subtract, void *scratch, cudaStream_t s) {
+                           int subtract, void *scratch, cudaStream_t s, const int *ncols_dev) {
     if (ncols <= 0) return cudaSuccess;
     static std::atomic<uint64_t> attr{0};
     smem_attr_once(trmv_oz_kernel, (int)OzSmem::bytes, attr);
@@ -460,16 +466,16 @@ cudaError_t launch_trmv_oz(const pseudo_ctx *h, int lower, const int *cols, cons
     const int64_t tiles = (ncols + OZ_NC - 1) / OZ_NC;
     int *fx = (int *)p;
     __nv_bfloat16 *img = (__nv_bfloat16 *)(p + ((tiles * OZ_NC * sizeof(int) + 255) & ~(size_t)255));
-    note_launch(); oz_colexp_kernel<<<(ncols + 31) / 32, 256, 0, s>>>(X, n, ldx, cols, ncols, fx);
+    note_launch(); oz_colexp_kernel<<<(ncols + 31) / 32, 256, 0, s>>>(X, n, ldx, cols, ncols, ncols_dev, fx);
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    note_launch(); oz_slice_b_kernel<<<nsm * 8, 256, 0, s>>>(X, n, n_pad, ldx, cols, ncols, fx, img);
+    note_launch(); oz_slice_b_kernel<<<nsm * 8, 256, 0, s>>>(X, n, n_pad, ldx, cols, ncols, ncols_dev, fx, img);
     const unsigned grid = (unsigned)(tiles * (n_pad / OZ_CR));
     note_launch();
     trmv_oz_kernel<<<grid, OZ_TH, OzSmem::bytes, s>>>((const __nv_bfloat16 *)(lower ? h->ozA_L : h->ozA_U), lower ? h->ozE_L : h->ozE_U, img, fx,
-                                                      n, n_pad, lower, cols, zc, ncols, X, ldx, B, ldb, Y, ldy,
-                                                      subtract, h->dev_err, h->wait_ns);
+                                                      n, n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, B, ldb,
+                                                      Y, ldy, subtract, h->dev_err, h->wait_ns);
     return cudaGetLastError();
 }
 

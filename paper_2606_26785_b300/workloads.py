@@ -22,6 +22,16 @@ standard-normal block followed by an imaginary n x n block, row-major):
   drawn with ``seed``, matrix i = ``gaussian(n_i, 100*seed + i)``.
 * ``grid(...)``: equispaced Cartesian grid, endpoints included in both axes,
   flattened as z[iy*nx + ix] = x[ix] + i*y[iy].
+* ``rect_gaussian(n, m, seed)``: rectangular m x n, entries (A + iB)/sqrt(n).
+* ``toeplitz_folding(n, m)``: the m x n section (m >= 2n) of the banded
+  Toeplitz operator with superdiagonal 1 and subdiagonal 0.25 (a matrix
+  folding: a rectangular truncation of an infinite matrix, Sec. 1).
+
+For a rectangular C (m >= 2n), ``rect_reduce`` is the preliminary reduction
+of SM2.2 followed by two more unitary steps that keep the singular values of
+C - zI: C_l = Q_1 R_l (thin QR), C_u = U T U^H (Schur), R_l U = Q_2 B (QR), so
+that [T - zI; B] = diag(U^H, Q_2^H) [C_u - zI; R_l] U with T and B upper
+triangular; the library takes the 2n x n pencil [T; B].
 """
 from __future__ import annotations
 
@@ -104,6 +114,41 @@ def schur(C: np.ndarray):
     return T, Q, err
 
 
+def rect_gaussian(n: int, m: int, seed: int) -> np.ndarray:
+    return _complex_normal(_rng(seed), (m, n)) / math.sqrt(n)
+
+
+def toeplitz_folding(n: int, m: int) -> np.ndarray:
+    C = np.zeros((m, n), dtype=np.complex128)
+    i = np.arange(n - 1)
+    C[i, i + 1] = 1.0
+    i = np.arange(min(n, m - 1))
+    C[i + 1, i] = 0.25
+    return C
+
+
+def rect_reduce(C: np.ndarray):
+    """The 2n x n pencil [T; B] of a rectangular C (m >= 2n rows): T and B upper
+    triangular with sigma([T - zI; B]) = sigma(C - zI) for every z, and the
+    backward error of the three factorisations (sum of their Frobenius-norm
+    residuals).  One-time host work before the method, never timed with it."""
+    import scipy.linalg
+
+    C = np.asarray(C, dtype=np.complex128)
+    m, n = C.shape
+    if m < 2 * n:
+        raise ValueError("need m >= 2n")
+    Cu, Cl = C[:n], C[n:]
+    Q1, Rl = np.linalg.qr(Cl, mode="reduced")
+    T, U = scipy.linalg.schur(Cu, output="complex")
+    T = np.triu(T)
+    Q2, B = np.linalg.qr(Rl @ U)
+    B = np.triu(B)
+    err = (np.linalg.norm(Cu - (U @ T) @ U.conj().T) + np.linalg.norm(Cl - Q1 @ Rl)
+           + np.linalg.norm(Rl @ U - Q2 @ B))
+    return np.vstack([T, B]), float(err)
+
+
 @dataclass
 class Workload:
     """One synthetic problem: the dense matrix C the oracle sees, the Schur
@@ -120,7 +165,7 @@ class Workload:
 
     @property
     def n(self) -> int:
-        return self.T.shape[0]
+        return self.T.shape[1]
 
 
 def make(name: str, nx: int | None = None, ny: int | None = None, n: int | None = None) -> Workload:
@@ -151,6 +196,17 @@ def make(name: str, nx: int | None = None, ny: int | None = None, n: int | None 
         nx = nx or 500
         ny = ny or 500
         z = grid(-1.5, 1.5, -1.0, 1.0, nx, ny)
+    elif name in ("rect_gaussian", "toeplitz_folding"):
+        if name == "rect_gaussian":
+            n = n or 150
+            C = rect_gaussian(n, 2 * n + 37, 7)
+            z = grid(-1.5, 1.5, -1.5, 1.5, nx or 40, ny or 40)
+        else:
+            n = n or 120
+            C = toeplitz_folding(n, 2 * n)
+            z = grid(-1.5, 1.5, -1.0, 1.0, nx or 40, ny or 40)
+        M, err = rect_reduce(C)
+        return Workload(name, C, M, z, nx or 40, ny or 40, err, {})
     else:
         raise ValueError(f"unknown workload {name!r}")
     T, _, err = schur(C)

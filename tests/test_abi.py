@@ -65,13 +65,16 @@ def test_argument_errors_are_reported_before_any_device_work():
     vp, c64 = ctypes.c_void_p, ctypes.c_int64
     buf = (ctypes.c_double * 8)()
     h = vp()
-    # pseudo_create: NULL out, NULL T, rectangular, n out of range, ldT < n
+    # pseudo_create: NULL out, NULL T, rows neither n nor 2n, n out of range,
+    # ldT < m (square and stacked pencil)
     assert lib.pseudo_create(buf, c64(2), c64(2), c64(2), 1, None, None) == _abi.ERR_ARG
     assert lib.pseudo_create(None, c64(2), c64(2), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
-    assert lib.pseudo_create(buf, c64(4), c64(4), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_UNSUPPORTED
-    assert b"rectangular" in lib.pseudo_last_error()
+    for m in (1, 3, 5, 8):
+        assert lib.pseudo_create(buf, c64(8), c64(m), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_UNSUPPORTED
+        assert b"pencil" in lib.pseudo_last_error()
     assert lib.pseudo_create(buf, c64(0), c64(0), c64(0), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
     assert lib.pseudo_create(buf, c64(1), c64(2), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
+    assert lib.pseudo_create(buf, c64(3), c64(4), c64(2), 1, None, ctypes.byref(h)) == _abi.ERR_ARG
     assert h.value is None
     o = _abi.Opts()
     assert lib.pseudo_opts_default(None) == _abi.ERR_ARG
@@ -124,12 +127,12 @@ def test_last_error_is_per_thread():
     def other():
         buf = (ctypes.c_double * 8)()
         h = ctypes.c_void_p()
-        seen["rc"] = lib.pseudo_create(buf, ctypes.c_int64(4), ctypes.c_int64(4), ctypes.c_int64(2), 1, None,
+        seen["rc"] = lib.pseudo_create(buf, ctypes.c_int64(4), ctypes.c_int64(3), ctypes.c_int64(2), 1, None,
                                        ctypes.byref(h))
         seen["msg"] = lib.pseudo_last_error()
 
     t = threading.Thread(target=other)
     t.start()
     t.join()
-    assert seen["rc"] == _abi.ERR_UNSUPPORTED and b"rectangular" in seen["msg"]
+    assert seen["rc"] == _abi.ERR_UNSUPPORTED and b"pencil" in seen["msg"]
     assert lib.pseudo_last_error() == mine and b"NULL" in mine

@@ -117,3 +117,51 @@ def test_grid_entry_matches_single_point_and_threads():
 def test_membership_is_strict():
     w = oracle.membership([0.1, 0.05, 1e-3], [0.1, 0.01])
     assert list(w) == [0b00, 0b01, 0b11]
+
+
+# ------------------------------------------------- rectangular C (m > n, Sec. 1)
+# For C in C^{m x n}, m >= n, the shift uses the m x n rectangular identity:
+# only the leading n x n block is shifted.
+
+@pytest.mark.parametrize("m,n", [(2, 1), (7, 3), (12, 5), (9, 4)])
+def test_rectangular_orthogonal_columns_closed_form(m, n):
+    # C = [D; E; 0] with D, E diagonal: column j of C - zI is (d_j - z) e_j +
+    # e_j e_{n+j}, so the columns are orthogonal and sigma_j = sqrt(|d_j - z|^2 +
+    # |e_j|^2).  A shift applied to the wrong rows, or to all m rows, fails this.
+    rng = np.random.default_rng(m * 10 + n)
+    d = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    e = np.zeros(n, dtype=complex)
+    k = min(n, m - n)
+    e[:k] = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    C = np.zeros((m, n), dtype=complex)
+    C[np.arange(n), np.arange(n)] = d
+    C[n + np.arange(k), np.arange(k)] = e[:k]
+    for z in [0.3 - 0.1j, d[0], -1.0 + 2.0j]:
+        s, _ = oracle.singular_values(C, z)
+        ref = np.sort(np.sqrt(np.abs(d - z) ** 2 + np.abs(e) ** 2))
+        assert np.max(np.abs(s - ref)) <= 64 * m * 2.2e-16 * max(1.0, ref.max())
+
+
+def test_rectangular_zero_bottom_is_the_square_normal_case():
+    # C = [Q diag(lam) Q^H; 0]: the zero rows change nothing, sigma = |lam - z|
+    rng = np.random.default_rng(5)
+    n = 6
+    lam = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    Q = _rand_unitary(n, rng)
+    C = np.vstack([Q @ np.diag(lam) @ Q.conj().T, np.zeros((2 * n + 1, n))])
+    for z in [0.2 + 0.4j, lam[2] + 1e-6]:
+        s, _ = oracle.singular_values(C, z)
+        assert np.max(np.abs(s - np.sort(np.abs(lam - z)))) <= 1e-13 * max(1.0, np.abs(lam - z).max())
+
+
+@pytest.mark.parametrize("m,n", [(4, 2), (9, 4), (20, 7)])
+def test_rectangular_matches_library_svd(m, n):
+    # a library SVD of the explicitly shifted matrix is an independent check
+    rng = np.random.default_rng(100 + m)
+    C = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+    for z in [0.0, 1.0 - 0.5j]:
+        A = C.copy()
+        A[np.arange(n), np.arange(n)] -= z
+        ref = np.sort(np.linalg.svd(A, compute_uv=False))
+        s, _ = oracle.singular_values(C, z)
+        assert np.max(np.abs(s - ref)) <= 1e-13 * ref.max()

@@ -1,5 +1,6 @@
 """Host-side input generators: shapes, recipes and determinism."""
 import numpy as np
+import pytest
 
 from paper_2606_26785_b300 import workloads
 
@@ -33,3 +34,29 @@ def test_triangular_recipe():
 def test_batch_sizes_range():
     s = workloads.gaussian_batch_sizes(64, 40)
     assert len(s) == 64 and min(s) >= 256 and max(s) <= 2048
+
+
+@pytest.mark.parametrize("name,n", [("rect_gaussian", 12), ("toeplitz_folding", 15)])
+def test_rect_reduce_keeps_singular_values(name, n):
+    """The host reduction of a rectangular C (SM2.2 plus a Schur form of the
+    top block and a QR of R_l U): [T; B] is 2n x n with both blocks upper
+    triangular, and sigma([T - zI; B]) = sigma(C - zI) -- both sides by the
+    oracle, within the reduction's backward error."""
+    import oracle
+
+    W = workloads.make(name, n=n, nx=3, ny=3)
+    M = W.T
+    assert M.shape == (2 * n, n)
+    assert np.all(np.tril(M[:n], -1) == 0) and np.all(np.tril(M[n:], -1) == 0)
+    assert W.schur_err < 1e-12 * max(1.0, np.linalg.norm(W.C))
+    for z in W.z:
+        a, _ = oracle.singular_values(W.C, z)
+        b, _ = oracle.singular_values(M, z)
+        assert np.max(np.abs(a - b)) <= 8 * W.schur_err + 1e-13 * a.max()
+
+
+def test_toeplitz_folding_recipe():
+    C = workloads.toeplitz_folding(4, 8)
+    assert C.shape == (8, 4)
+    assert C[0, 1] == 1 and C[2, 3] == 1 and C[1, 0] == 0.25 and C[4, 3] == 0.25
+    assert np.count_nonzero(C) == 3 + 4
