@@ -225,8 +225,14 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
  *                 pointers, each as in pseudo_grid (res/flags/member arrays
  *                 and their entries may be NULL).
  *   npts        : host array of nmat point counts (0 allowed).
- *   eps_levels, neps, o : shared by all matrices, as in pseudo_grid.
+ *   eps_levels, neps, o : shared by all matrices, as in pseudo_grid, except that
+ *                 every matrix's inverse-Lanczos loop is driven from its worker
+ *                 thread (o->device_loop is not used): replayed conditional-node
+ *                 graphs on the workers' streams overlapped less on the device
+ *                 than host-driven loops did (measured).
  *   workspace   : device memory of >= pseudo_grid_batch_workspace_bytes(...).
+ * Matrices are assigned to the workers by a fixed rule (largest first, balanced
+ * by n^2 x npts), so repeated calls repeat the assignment.
  * Work is ordered after prior work on `stream`; later work on `stream` waits
  * for all of it.  Returns the largest non-negative status over the matrices,
  * or the first error (the message names the matrix). */

@@ -34,6 +34,10 @@ namespace pseudo {
 struct LancLayout {
     int S = 0, F = 0, mmax = 0;
     bool fp32 = false;
+    // the FP64 pass of mixed precision: the Rayleigh quotients and residuals of
+    // its finished points use the tensor-core double-single-accurate product
+    // (its sigma is the FP64 Lanczos value; the product only feeds res)
+    bool ds_products = false;
     void *Q = nullptr, *W = nullptr, *xs = nullptr;
     double *alpha = nullptr, *beta = nullptr, *svec = nullptr, *theta = nullptr;
     double2 *Hp = nullptr;                           // Gram-Schmidt coefficients, S x (mmax+1)
@@ -111,9 +115,10 @@ static int choose_slots(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, bool 
 }
 
 static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c, LancLayout &L, bool on_host,
-                        bool fp32, int slots = 0) {
+                        bool fp32, int slots = 0, bool ds_products = false) {
     memset(&L, 0, sizeof L);  // its bytes (padding included) key the graph cache
     L.fp32 = fp32;
+    L.ds_products = ds_products && h->ozA_U;
     L.mmax = o->maxiter_lanczos;
     L.S = slots > 0 ? (int)std::min<int64_t>(slots, npts) : choose_slots(h, o, npts, L.fp32, L.mmax);
     L.F = 2 * L.S;
@@ -161,6 +166,7 @@ static void lanc_layout(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carve
     L.fin_pt = c.get<int>(F);
     L.fin_conv = c.get<int>(F);
     L.mask = c.get<int>(F);
+    if (L.ds_products) L.oz = c.take(oz_scratch_bytes(h->n_pad, F));
     if (L.fp32) {
         L.X64 = c.get<double2>(n * F);
         L.R64 = c.get<double2>(n * F);
@@ -200,7 +206,7 @@ void invlanc_carve(pseudo_ctx *h, const pseudo_opts *o, int64_t npts, Carver &c,
     LancLayout L, Lfb;
     const bool mixed = o->precision == PSEUDO_MIXED;
     lanc_layout(h, o, npts, c, L, o->io_host != 0, mixed);
-    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS, true);
 }
 
 // Refine (mixed) and finalise the P finished points held in columns [0, P)
@@ -232,7 +238,7 @@ static int finish_batch(pseudo_ctx *h, const pseudo_opts *o, LancLayout &L, int 
         cudaMemcpyAsync(L.Ufin, L.X64, (size_t)n * F * sizeof(double2), cudaMemcpyDeviceToDevice, s);
     }
     // Rayleigh quotient and residual of the returned vectors
-    const bool hp = L.fp32;
+    const bool hp = L.fp32 || L.ds_products;
     const int kc = hp ? PSEUDO_K_TRMV_DS : PSEUDO_K_TRMV64;
     int k0 = kp_begin(h, s);
     if (h->rect) {
@@ -738,7 +744,7 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     LancLayout L, Lfb;
     const bool mixed = o->precision == PSEUDO_MIXED;
     lanc_layout(h, o, io.npts, c, L, io.on_host, mixed);
-    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS);
+    if (mixed) lanc_layout(h, o, L.CH, c, Lfb, false, false, FB_SLOTS, true);
     if (c.overflow) return set_err(PSEUDO_ERR_WORKSPACE, "workspace too small");
     const int64_t npts = io.npts;
     cudaError_t e;
