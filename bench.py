@@ -337,6 +337,10 @@ def main():
     ap.add_argument("--extras-budget", type=float, default=480.0,
                     help="seconds of wall time the comparison paths may take; the ones that would start later are "
                          "reported as skipped")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the inverse-Lanczos loop from the host (device_loop = 0): the same kernels as plain "
+                         "launches, which a kernel profiler sees one by one (it does not profile the kernels of "
+                         "graphs with conditional nodes)")
     ap.add_argument("--accuracy-full", action="store_true",
                     help="also run the FP64 path on every grid point and compare (about ten minutes at n = 8000)")
     ap.add_argument("--profile-kernel", choices=["solve", "product", "solve_ds", "solve_fp64"],
@@ -430,7 +434,7 @@ def main():
         return
     prec = p.MIXED if args.precision == "mixed" else p.FP64
     rtol = 1e-8 if prec == p.MIXED else 1e-10
-    opts = p.default_opts(mode=p.INVLANC, precision=prec, rtol=rtol)
+    opts = p.default_opts(mode=p.INVLANC, precision=prec, rtol=rtol, device_loop=0 if args.host_loop else 1)
     npts = W.z.size
     NB = max(1, min(args.batches, npts))
     bidx = [np.arange(b, npts, NB) for b in range(NB)]

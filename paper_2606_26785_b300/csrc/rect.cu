@@ -33,6 +33,22 @@ int64_t rect_packed_size(int n) { return (int64_t)n * (n + 1) / 2; }
 // packed column-major upper triangle: (i, j), i <= j, at j (j + 1) / 2 + i
 __device__ __forceinline__ int64_t up_idx(int i, int j) { return (int64_t)j * (j + 1) / 2 + i; }
 
+// acc += conj(a) b in four fused multiply-adds
+__device__ __forceinline__ void cfmac(double2 &acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// acc -= conj(a) b
+__device__ __forceinline__ void cfmsc(double2 &acc, double2 a, double2 b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
 __device__ __forceinline__ double2 warp_sum_c(double2 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -122,7 +138,7 @@ rect_qr_kernel(const double2 *__restrict__ M, int64_t ldm, int n, const int *__r
             for (int j = k + 1 + warp; j < n; j += QR_WARPS) {
                 double2 *bc = Bw + up_idx(0, j);
                 double2 w = make_double2(0.0, 0.0);
-                for (int i = lane; i <= k; i += 32) w = cadd(w, cmulc(vs[i], bc[i]));
+                for (int i = lane; i <= k; i += 32) cfmac(w, vs[i], bc[i]);
                 w = warp_sum_c(w);
                 double2 *rk = R + up_idx(k, j);
                 w = cadd(w, *rk);
@@ -139,14 +155,16 @@ rect_qr_kernel(const double2 *__restrict__ M, int64_t ldm, int n, const int *__r
         for (int j = k + 1 + tid; j < n; j += QR_THREADS) {
             double2 *bc = Bw + up_idx(0, j);
             double2 *rk = R + up_idx(k, j);
-            double2 w0 = *rk, w1 = make_double2(0.0, 0.0);
+            double2 w0 = *rk, w1 = make_double2(0.0, 0.0), w2 = w1, w3 = w1;
             int i = 0;
-            for (; i + 1 <= k; i += 2) {  // two partial sums shorten the dependence chain
-                w0 = cadd(w0, cmulc(vs[i], bc[i]));
-                w1 = cadd(w1, cmulc(vs[i + 1], bc[i + 1]));
+            for (; i + 3 <= k; i += 4) {  // four partial sums: the thread's chain is the latency
+                cfmac(w0, vs[i], bc[i]);
+                cfmac(w1, vs[i + 1], bc[i + 1]);
+                cfmac(w2, vs[i + 2], bc[i + 2]);
+                cfmac(w3, vs[i + 3], bc[i + 3]);
             }
-            if (i <= k) w0 = cadd(w0, cmulc(vs[i], bc[i]));
-            const double2 tw = cmul(ctau, cadd(w0, w1));
+            for (; i <= k; ++i) cfmac(w0, vs[i], bc[i]);
+            const double2 tw = cmul(ctau, cadd(cadd(w0, w1), cadd(w2, w3)));
             for (i = 0; i <= k; ++i) cfms(bc[i], tw, vs[i]);
             *rk = csub(*rk, tw);
         }
@@ -201,17 +219,17 @@ rect_solve_kernel(const double2 *__restrict__ Rs, int n, int lower, const int *_
             if (i < n) {
                 int j = 0;
                 for (; j + 1 < i0; j += 2) {
-                    s0 = cadd(s0, cmulc(col[j], y[j]));
-                    s1 = cadd(s1, cmulc(col[j + 1], y[j + 1]));
+                    cfmac(s0, col[j], y[j]);
+                    cfmac(s1, col[j + 1], y[j + 1]);
                 }
-                if (j < i0) s0 = cadd(s0, cmulc(col[j], y[j]));
+                if (j < i0) cfmac(s0, col[j], y[j]);
             }
             double2 yi = i < n ? csub(y[i], cadd(s0, s1)) : make_double2(0.0, 0.0);
             const int tb = min(32, n - i0);
             for (int t = 0; t < tb; ++t) {
                 if (lane == t) yi = cmulc(col[i], yi);  // conj(1 / R(i, i)) y_i
                 const double2 yt = shfl_c(yi, t);
-                if (lane > t && i < n) yi = csub(yi, cmulc(col[i0 + t], yt));
+                if (lane > t && i < n) cfmsc(yi, col[i0 + t], yt);
             }
             if (i < n) y[i] = yi;
             __syncwarp();
