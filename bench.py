@@ -199,11 +199,16 @@ def _tf32x3_tflops(peaks):
 
 
 # DRAM bytes (read + write) per column of a launch, from one ncu capture of each
-# tensor-core kernel on 4,096 columns of the bench matrix (bench.py
-# --profile-kernel solve|product); traffic grows with the columns of a launch
-# (A re-reads per column tile, B images per column group).
+# tensor-core kernel on 4,096 columns (bench.py --profile-kernel solve|product
+# [--profile-n 4000]); traffic grows with the columns of a launch (A re-reads
+# per column group, B images per column group).  n = 2000: the narrow solve
+# (16 columns per CTA) and the product on the Gaussian matrix.  n = 8000: the
+# wide solve (32 columns per CTA) captured on the leading 4000 x 4000 block of
+# the triangular matrix and scaled by (8000 / 4000)^2, the growth of the A
+# stream every CTA reads; a lower estimate, since the larger A misses L2 more.
 DRAM_BYTES_PER_COLUMN = {("trsv32", 2000): (1.694567e9 + 0.3204608e9) / 4096,
-                         ("trmv_ds", 2000): (1.939070e9 + 0.111231e9) / 4096}
+                         ("trmv_ds", 2000): (1.939070e9 + 0.111231e9) / 4096,
+                         ("trsv32", 8000): (8.017367296e9 + 0.663716864e9) / 4096 * 4.0}
 
 
 def _traffic(kernel, n, cols):

@@ -1,6 +1,12 @@
 """Build the CUDA library libpseudo_b300.so for sm_103a (in-tree).
 
     python -m paper_2606_26785_b300.build
+    python -m paper_2606_26785_b300.build --define TC_WIDE_MIN_NPAD=0 --out /tmp/wide/libpseudo_b300.so
+
+``--define`` passes compile-time tuning constants of the kernels (for example
+``TC_WIDE_MIN_NPAD``, the padded order from which the tensor-core solve runs
+32 columns per CTA); such builds go to ``--out`` for side-by-side timing
+(``probe/solve_sweep.py --lib``) and never replace the in-tree library.
 """
 from __future__ import annotations
 
@@ -29,13 +35,16 @@ def _stale() -> bool:
     return any(p.stat().st_mtime > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> Path:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, defines=(), out: Path | None = None) -> Path:
+    lib = LIB if out is None else Path(out).resolve()
+    if lib == LIB and defines:
+        raise ValueError("builds with --define go to their own --out path")
+    if lib == LIB and not force and not _stale():
         return LIB
-    objdir = PKG / "_build"
-    objdir.mkdir(exist_ok=True)
+    objdir = PKG / "_build" if lib == LIB else lib.parent / "_build"
+    objdir.mkdir(parents=True, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(ROOT / "include"),
-                    "--expt-relaxed-constexpr"]
+                    "--expt-relaxed-constexpr"] + ["-D" + d for d in defines]
     if verbose:
         flags += ["-Xptxas", "-v"]
     objs = []
@@ -54,12 +63,19 @@ def build(force: bool = False, verbose: bool = False) -> Path:
             failed = True
     if failed:
         raise RuntimeError("nvcc failed")
-    tmp = LIB.with_suffix(".so.tmp")
+    tmp = lib.with_suffix(".so.tmp")
     subprocess.run([NVCC, "-shared", *ARCH, "-o", str(tmp), *map(str, objs), "-lcudart"], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("-v", dest="verbose", action="store_true")
+    ap.add_argument("--define", action="append", default=[], help="NAME=VALUE, a compile-time tuning constant")
+    ap.add_argument("--out", type=Path, default=None, help="library path of a build with --define")
+    a = ap.parse_args()
+    print(build(force=a.force, verbose=a.verbose, defines=a.define, out=a.out))

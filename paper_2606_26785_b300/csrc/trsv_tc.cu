@@ -121,11 +121,26 @@ void launch_pack_tc(const double2 *T, int64_t ldT, int n, int n_pad, float *AU, 
 // Hand-offs are mbarriers; every wait is bounded and gives up on a shared
 // abort flag.  Warps 2-3 only take part in set-up and tear-down.
 namespace {
-#ifndef TC_NS
-#define TC_NS 2   // 2 stages: two CTAs fit on an SM (shared memory, 128 registers)
+// Two configurations of (columns per CTA, ring stages):
+//   narrow: 16 columns, 2 stages of 40 KB, two CTAs per SM;
+//   wide:   32 columns, 4 stages of 48 KB, one CTA per SM; the reciprocal
+//           diagonal shares the accumulator's turnaround buffer to make room.
+// At large orders a CTA's sweep is set by its stream of chunks (about 0.6 us
+// per chunk whether 37 or 148 CTAs run, and whether the ring has 3 or 4
+// stages), and a wide chunk carries twice the columns for 1.2x the bytes, so a
+// wide CTA finishes its 32 columns sooner than a narrow CTA its 16: measured
+// at n = 8000, 1.16x (1,184 columns) to 1.31x (9,472 columns) faster; at
+// n = 4000, 1.12x.  At small orders the 128-step diagonal-block solves set
+// the pace instead, and a wide CTA has twice the columns per diagonal warp:
+// at n = 2048 the narrow form is 1.2-1.3x faster, so handles below
+// TC_WIDE_MIN_NPAD keep it.
+#ifndef TC_WIDE_STAGES
+#define TC_WIDE_STAGES 4   // ring stages of the wide form (3 measured the same; 4 is the most that fits)
 #endif
-#ifndef TC_NC
-#define TC_NC 16
+constexpr int NC_NARROW = 16, NS_NARROW = 2;
+constexpr int NC_WIDE = 32, NS_WIDE = TC_WIDE_STAGES;
+#ifndef TC_WIDE_MIN_NPAD
+#define TC_WIDE_MIN_NPAD 4096   // padded order from which a handle uses the wide configuration
 #endif
 #ifndef TC_NACC
 #define TC_NACC 1   // partial accumulators per panel (more did not pay off when measured)
@@ -136,7 +151,7 @@ namespace {
 #ifndef TC_A_EVICT_LAST
 #define TC_A_EVICT_LAST 1   // A chunks copied with an L2 evict-last policy (every CTA streams them)
 #endif
-constexpr int NS = TC_NS, TC_THREADS = 256;
+constexpr int TC_THREADS = 256;
 constexpr int BAR_DIAG = 1;  // named barrier of the diagonal warps (0 is __syncthreads)
 
 __device__ __forceinline__ void named_bar(int id, int count) {
@@ -158,14 +173,18 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
 }
 }  // namespace
 
-template <int NC>
+template <int NC, int NS>
 struct TcSmem {
+    // the wide form keeps 1 / (t_ii - z_c) in the turnaround buffer once the
+    // accumulator has been read out of it; the narrow form has its own array
+    static constexpr bool dinv_shared = NC >= 32;
     static constexpr int NR = 2 * NC;            // real N of the MMA
     static constexpr int B_SPLIT = NR * KR;      // floats
     static constexpr int B_IMG = 2 * B_SPLIT;    // hi + lo
     static constexpr size_t stage = (size_t)(A_CHUNK + B_IMG) * sizeof(float);
     // ring of stages, then the turned-around accumulator and 1 / (t_ii - z_c)
-    static constexpr size_t diag = (size_t)MB * (2 * NC + 1) * sizeof(float) + (size_t)MB * NC * sizeof(float2);
+    static constexpr size_t diag =
+        (size_t)MB * (2 * NC + 1) * sizeof(float) + (dinv_shared ? 0 : (size_t)MB * NC * sizeof(float2));
     static constexpr size_t bytes = NS * stage + diag + 128;  // + alignment slack
     // two panels in flight, TC_NACC partial accumulators each (power of two >= 32 columns)
     static constexpr uint32_t acc_cols = 2 * TC_NACC * NR;
@@ -173,22 +192,25 @@ struct TcSmem {
                                           : acc_cols <= 256 ? 256 : 512;
 };
 
-// Scratch of the solves for ncols columns in groups of 16: the compact copy of
-// each group's solution (the CUDA-core kernel) followed by the B'' images of
-// every 16-row chunk of each group (the tensor-core kernel).
+// Scratch of the solves for ncols columns: the compact copy of each column
+// group's solution (the CUDA-core kernel, groups of 16) followed by the B''
+// images of every 16-row chunk of each group (the tensor-core kernel, groups
+// of 16 or 32 columns).  Both cost 40 bytes per column and row, so the layout
+// of the wider groups (ncols rounded up to 32) covers every kernel.
 size_t trsv32_scratch_bytes(int64_t n_pad, int64_t ncols) {
-    const int64_t groups = (ncols + TC_NC - 1) / TC_NC;  // TC_NC is a multiple of the CUDA-core group (16)
-    return (size_t)groups * n_pad * TC_NC * sizeof(float2) +
-           (size_t)groups * (n_pad / KC) * TcSmem<TC_NC>::B_IMG * sizeof(float);
+    static_assert(NC_WIDE % NC_NARROW == 0 && NC_NARROW % 16 == 0, "groups nest");
+    const int64_t groups = (ncols + NC_WIDE - 1) / NC_WIDE;
+    return (size_t)groups * n_pad * NC_WIDE * sizeof(float2) +
+           (size_t)groups * (n_pad / KC) * TcSmem<NC_WIDE, NS_WIDE>::B_IMG * sizeof(float);
 }
 
-template <int NC>
-__global__ void __launch_bounds__(TC_THREADS, TC_NS <= 2 ? 2 : 1)
+template <int NC, int NS>
+__global__ void __launch_bounds__(TC_THREADS, NS <= 2 && NC <= 16 ? 2 : 1)
 trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
                const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err,
-               uint64_t wait_ns) {
-    using L = TcSmem<NC>;
+               uint64_t wait_ns, int cmin, int cmax) {
+    using L = TcSmem<NC, NS>;
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
     static_assert(NR % 32 == 0, "the diagonal warps read the accumulator in 32-column pieces");
@@ -204,7 +226,9 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
 
     const int ncols = ncols_dev ? *ncols_dev : ncols_host;
     const int g = blockIdx.x;
-    if (g * NC >= ncols) return;
+    // [cmin, cmax]: the live counts this configuration serves (one of the
+    // launches that cover a count known only on the device)
+    if (g * NC >= ncols || ncols < cmin || ncols > cmax) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float *sbuf = reinterpret_cast<float *>(smem_raw + ((128 - (tc::smem_u32(smem_raw) & 127)) & 127));
     constexpr int STAGE_F = A_CHUNK + L::B_IMG;  // floats per stage: A'' hi, A'' lo, B'' hi, B'' lo
@@ -322,7 +346,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
         const int i = tid - 128, dw = warp - 4;
         const int cw0 = dw * CPW;
         float *Dsm = sbuf + NS * STAGE_F;                 // [MB][2 NC + 1]
-        float2 *s_dinv = reinterpret_cast<float2 *>(Dsm + MB * (2 * NC + 1));  // [MB][NC]
+        float2 *s_dinv = reinterpret_cast<float2 *>(L::dinv_shared ? Dsm : Dsm + MB * (2 * NC + 1));  // [MB][NC]
         for (int p = 0; p < P; ++p) {
             const int J = lower ? p : P - 1 - p;
             const int buf = p & 1;
@@ -352,9 +376,12 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
 #pragma unroll
                     for (int u = 0; u < 32; ++u) Dsm[i * (2 * NC + 1) + piece * 32 + u] = d[u];
                 }
-                const float2 tii = DJ[i * MB + i];
+                if constexpr (!L::dinv_shared) {
+                    const float2 tii = DJ[i * MB + i];
 #pragma unroll
-                for (int c = 0; c < NC; ++c) s_dinv[i * NC + c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+                    for (int c = 0; c < NC; ++c)
+                        s_dinv[i * NC + c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+                }
             }
             tc::tc_fence_before();
             named_bar(BAR_DIAG, 128);
@@ -371,6 +398,16 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                     if (row < n && s_col[col] >= 0) b = X[(int64_t)row * ldx + s_col[col]];
                     r[k][c] = make_float2(b.x - Dsm[rl * (2 * NC + 1) + col], b.y - Dsm[rl * (2 * NC + 1) + NC + col]);
                 }
+            }
+            if constexpr (L::dinv_shared) {
+                // every warp has read its part of the accumulator: the buffer
+                // now takes the reciprocal diagonal (row i, all NC columns)
+                named_bar(BAR_DIAG, 128);
+                const float2 tii = DJ[i * MB + i];
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    s_dinv[i * NC + c] = crecip(make_float2(tii.x - s_z[c].x, tii.y - s_z[c].y));
+                named_bar(BAR_DIAG, 128);
             }
             // coefficient of x_j in this thread's rows, loaded PD steps ahead
             // (the stored blocks are zero where a row does not depend on x_j)
@@ -459,27 +496,32 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
     if (warp == 0) tc::tmem_dealloc(tmem, L::tmem_cols);
 }
 
-constexpr int NC_TC = TC_NC;
-int trsv_tc_group_width() { return NC_TC; }
+template <int NC, int NS>
+static cudaError_t launch_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
+                             const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s, int cmin,
+                             int cmax) {
+    using L = TcSmem<NC, NS>;
+    static std::atomic<uint64_t> attr{0};
+    smem_attr_once(trsv_tc_kernel<NC, NS>, (int)L::bytes, attr);
+    const int grid = (ncols + NC - 1) / NC;
+    if (grid == 0) return cudaSuccess;
+    note_launch();
+    trsv_tc_kernel<NC, NS><<<grid, TC_THREADS, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
+                                                             h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx,
+                                                             xs, h->dev_err, h->wait_ns, cmin, cmax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
-    using L = TcSmem<NC_TC>;
-    static std::atomic<uint64_t> attr{0};
-    smem_attr_once(trsv_tc_kernel<NC_TC>, (int)L::bytes, attr);
-    const int grid = (ncols + NC_TC - 1) / NC_TC;
-    if (grid == 0) return cudaSuccess;
-    note_launch();
-    trsv_tc_kernel<NC_TC><<<grid, TC_THREADS, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
-                                                      h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs,
-                                                      h->dev_err, h->wait_ns);
-    return cudaGetLastError();
+    if (h->n_pad >= TC_WIDE_MIN_NPAD)
+        return launch_tc<NC_WIDE, NS_WIDE>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s, 0, 0x7fffffff);
+    return launch_tc<NC_NARROW, NS_NARROW>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s, 0, 0x7fffffff);
 }
 
 cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                     const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
-    // the scratch (trsv32_scratch_bytes) covers both kernels' column groups
-    static_assert(NC_TC % 16 == 0, "tensor-core column groups are whole CUDA-core groups");
+    // the scratch (trsv32_scratch_bytes) covers every kernel's column groups
     if (h->fp32_solver == 0 && h->tcA_U)
         return launch_trsv_tc(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
