@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(TC_THREADS, NS <= 2 && NC <= 16 ? 2 : 1)
 trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk, int n, int n_pad, int lower,
                const int *__restrict__ cols, const double2 *__restrict__ zc, int ncols_host,
                const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err,
-               uint64_t wait_ns, int cmin, int cmax) {
+               uint64_t wait_ns) {
     using L = TcSmem<NC, NS>;
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
@@ -226,9 +226,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
 
     const int ncols = ncols_dev ? *ncols_dev : ncols_host;
     const int g = blockIdx.x;
-    // [cmin, cmax]: the live counts this configuration serves (one of the
-    // launches that cover a count known only on the device)
-    if (g * NC >= ncols || ncols < cmin || ncols > cmax) return;
+    if (g * NC >= ncols) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float *sbuf = reinterpret_cast<float *>(smem_raw + ((128 - (tc::smem_u32(smem_raw) & 127)) & 127));
     constexpr int STAGE_F = A_CHUNK + L::B_IMG;  // floats per stage: A'' hi, A'' lo, B'' hi, B'' lo
@@ -498,8 +496,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
 
 template <int NC, int NS>
 static cudaError_t launch_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
-                             const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s, int cmin,
-                             int cmax) {
+                             const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
     using L = TcSmem<NC, NS>;
     static std::atomic<uint64_t> attr{0};
     smem_attr_once(trsv_tc_kernel<NC, NS>, (int)L::bytes, attr);
@@ -508,15 +505,15 @@ static cudaError_t launch_tc(const pseudo_ctx *h, int lower, const int *cols, co
     note_launch();
     trsv_tc_kernel<NC, NS><<<grid, TC_THREADS, L::bytes, s>>>(lower ? h->tcA_L : h->tcA_U, lower ? h->tcD_L : h->tcD_U,
                                                              h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx,
-                                                             xs, h->dev_err, h->wait_ns, cmin, cmax);
+                                                             xs, h->dev_err, h->wait_ns);
     return cudaGetLastError();
 }
 
 cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
     if (h->n_pad >= TC_WIDE_MIN_NPAD)
-        return launch_tc<NC_WIDE, NS_WIDE>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s, 0, 0x7fffffff);
-    return launch_tc<NC_NARROW, NS_NARROW>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s, 0, 0x7fffffff);
+        return launch_tc<NC_WIDE, NS_WIDE>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
+    return launch_tc<NC_NARROW, NS_NARROW>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
 }
 
 cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
