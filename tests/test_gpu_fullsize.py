@@ -1,7 +1,8 @@
 """Full-size parity on the dense complex Gaussian workload (n = 2000, seed 2,
 200 x 200 grid over [-1.5, 1.5]^2) in the launch configuration bench.py
 times, against stored oracle values at 32 sampled grid points
-(tests/golden/gaussian2000_samples.json, written by the oracle alone), plus
+(tests/golden/gaussian2000_samples.json, written by the oracle alone), with
+identical epsilon-membership there, plus
 the strongly nonnormal triangular workload (n = 8000, seed 3) where the mixed
 path is compared with the FP64 path at every point of a coarse sub-grid."""
 import json
@@ -30,20 +31,21 @@ def test_gaussian2000_full_grid(gauss, mode, precision, rtol):
 
     W, g = gauss
     h = p.Pseudo(W.T)
+    idx = np.array(g["index"])
     if mode == "invlanc":
-        z = W.z if precision == 1 else W.z[np.array(g["index"])]
+        z = W.z if precision == 1 else W.z[idx]
         out = h.grid(z, workloads.EPS_LEVELS, mode=p.INVLANC, precision=precision, rtol=rtol)
-        sig = out["sigma"].cpu().numpy()
+        sig, mem = out["sigma"].cpu().numpy(), out["member"].cpu().numpy()
         if precision == 1:
-            sig = sig[np.array(g["index"])]
+            sig, mem = sig[idx], mem[idx]
     else:
         out = h.grid(W.z, workloads.EPS_LEVELS, mode=p.RECYCLE, precision=precision, rtol=rtol, r=4, p_max=4,
                      grid_nx=W.nx, grid_ny=W.ny, batch_b=20)
-        sig = out["sigma"].cpu().numpy()[np.array(g["index"])]
+        sig, mem = out["sigma"].cpu().numpy()[idx], out["member"].cpu().numpy()[idx]
     rep = check_sigma(sig, np.array(g["sigma_ref"]), n=W.n, fro=g["fro_norm"], schur_err=W.schur_err,
-                      oracle_off=np.array(g["oracle_off"]), rtol=rtol)
+                      oracle_off=np.array(g["oracle_off"]), rtol=rtol, eps_levels=workloads.EPS_LEVELS, member=mem)
     print(mode, precision, rep, h.stats())
-    assert rep["n_bad"] == 0, rep
+    assert rep["n_bad"] == 0 and rep["member_mismatch"] == 0, rep
     h.close()
 
 
@@ -124,6 +126,7 @@ def test_toeplitz1200_mixed(mode, k):
         out = h.grid(z, workloads.EPS_LEVELS, mode=p.INVLANC, precision=p.MIXED, rtol=1e-8)
     sig = out["sigma"].cpu().numpy()[idx]
     flags = out["flags"].cpu().numpy()[idx]
+    mem = out["member"].cpu().numpy()[idx]
     ref = np.array(g["sigma_ref"])
     unconv = (flags & p._abi.PT_NOT_CONVERGED) != 0
     rel = np.abs(sig - ref) / ref
@@ -132,8 +135,9 @@ def test_toeplitz1200_mixed(mode, k):
     # converged (a cluster of nearly equal singular values the iteration caps
     # cannot resolve); such estimates stay upper bounds and close to sigma_min
     rep = check_sigma(sig[~unconv], ref[~unconv], n=g["n"], fro=g["fro_norm"], schur_err=err,
-                      oracle_off=np.array(g["oracle_off"])[~unconv], rtol=1e-8)
-    assert rep["n_bad"] == 0, rep
+                      oracle_off=np.array(g["oracle_off"])[~unconv], rtol=1e-8, eps_levels=workloads.EPS_LEVELS,
+                      member=mem[~unconv])
+    assert rep["n_bad"] == 0 and rep["member_mismatch"] == 0, rep
     assert np.all(sig[unconv] >= ref[unconv] * (1 - 1e-12)), rel[unconv]
     assert np.all(rel[unconv] <= 1e-3), rel[unconv]
     assert (~unconv).sum() >= len(ref) // 4, unconv
