@@ -49,7 +49,7 @@ def _stream_ptr(stream):
 class Pseudo:
     """Handle on one Schur factor T (n x n, upper triangular, complex128), or
     on a rectangular pencil [T; B] (2n x n, both blocks upper triangular; see
-    ``workloads.rect_reduce``)."""
+    ``workloads.rect_reduce``, which takes any C with m > n rows)."""
 
     def __init__(self, T, stream=None):
         torch = _torch()

@@ -26,12 +26,16 @@ standard-normal block followed by an imaginary n x n block, row-major):
 * ``toeplitz_folding(n, m)``: the m x n section (m >= 2n) of the banded
   Toeplitz operator with superdiagonal 1 and subdiagonal 0.25 (a matrix
   folding: a rectangular truncation of an infinite matrix, Sec. 1).
+* ``rect_gaussian_short``: a Gaussian C with n < m < 2n (m = n + 3n/8).
 
 For a rectangular C (m >= 2n), ``rect_reduce`` is the preliminary reduction
 of SM2.2 followed by two more unitary steps that keep the singular values of
 C - zI: C_l = Q_1 R_l (thin QR), C_u = U T U^H (Schur), R_l U = Q_2 B (QR), so
 that [T - zI; B] = diag(U^H, Q_2^H) [C_u - zI; R_l] U with T and B upper
-triangular; the library takes the 2n x n pencil [T; B].
+triangular; the library takes the 2n x n pencil [T; B].  With n < m < 2n,
+C is first extended by 2n - m zero rows: [C; 0] - z[I; 0] = [C - zI; 0] has
+the singular values of C - zI, and the extended matrix has m = 2n (B then
+has only m - n nonzero rows).
 """
 from __future__ import annotations
 
@@ -128,16 +132,19 @@ def toeplitz_folding(n: int, m: int) -> np.ndarray:
 
 
 def rect_reduce(C: np.ndarray):
-    """The 2n x n pencil [T; B] of a rectangular C (m >= 2n rows): T and B upper
+    """The 2n x n pencil [T; B] of a rectangular C (m > n rows): T and B upper
     triangular with sigma([T - zI; B]) = sigma(C - zI) for every z, and the
     backward error of the three factorisations (sum of their Frobenius-norm
-    residuals).  One-time host work before the method, never timed with it."""
+    residuals).  One-time host work before the method, never timed with it.
+    With m < 2n the rows of C are first extended by zeros to 2n."""
     import scipy.linalg
 
     C = np.asarray(C, dtype=np.complex128)
     m, n = C.shape
+    if m <= n:
+        raise ValueError("need m > n (a square C takes the Schur factor)")
     if m < 2 * n:
-        raise ValueError("need m >= 2n")
+        C = np.vstack([C, np.zeros((2 * n - m, n), dtype=np.complex128)])
     Cu, Cl = C[:n], C[n:]
     Q1, Rl = np.linalg.qr(Cl, mode="reduced")
     T, U = scipy.linalg.schur(Cu, output="complex")
@@ -196,10 +203,14 @@ def make(name: str, nx: int | None = None, ny: int | None = None, n: int | None 
         nx = nx or 500
         ny = ny or 500
         z = grid(-1.5, 1.5, -1.0, 1.0, nx, ny)
-    elif name in ("rect_gaussian", "toeplitz_folding"):
+    elif name in ("rect_gaussian", "toeplitz_folding", "rect_gaussian_short"):
         if name == "rect_gaussian":
             n = n or 150
             C = rect_gaussian(n, 2 * n + 37, 7)
+            z = grid(-1.5, 1.5, -1.5, 1.5, nx or 40, ny or 40)
+        elif name == "rect_gaussian_short":
+            n = n or 120
+            C = rect_gaussian(n, n + max(1, 3 * n // 8), 8)
             z = grid(-1.5, 1.5, -1.5, 1.5, nx or 40, ny or 40)
         else:
             n = n or 120

@@ -1,10 +1,12 @@
-"""Rectangular input, m >= 2n (SM2.2): FP64 inverse Lanczos on the 2n x n
+"""Rectangular input, m > n (SM2.2; a C with n < m < 2n is extended by zero
+rows to 2n): FP64 inverse Lanczos on the 2n x n
 pencil [T - zI; B] with one QR factorisation per point, against the oracle's
 Jacobi SVD of the ORIGINAL rectangular C - zI (m x n, rectangular identity).
 
 Workloads (seeded, paper_2606_26785_b300.workloads): a dense Gaussian
-C (n = 150, m = 2n + 37) and the m = 2n section of the banded Toeplitz
-operator (superdiagonal 1, subdiagonal 0.25; a matrix folding, Sec. 1), each on
+C (n = 150, m = 2n + 37), the m = 2n section of the banded Toeplitz
+operator (superdiagonal 1, subdiagonal 0.25; a matrix folding, Sec. 1), and a
+Gaussian with n < m < 2n (n = 120, m = 165, extended by zero rows), each on
 a 40 x 40 grid with every point compared at rtol 1e-10 under the pass rule of
 tests/parity.py, with identical epsilon-membership; a larger Gaussian
 (n = 600) at sampled points; and the zero-bottom case that reduces to the
@@ -31,7 +33,7 @@ def _parity(W, sig, member, ref, off, rtol=1e-10):
     return rep
 
 
-@pytest.mark.parametrize("name", ["rect_gaussian", "toeplitz_folding"])
+@pytest.mark.parametrize("name", ["rect_gaussian", "toeplitz_folding", "rect_gaussian_short"])
 def test_rect_full_grid(name):
     import paper_2606_26785_b300 as p
 

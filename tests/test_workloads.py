@@ -36,12 +36,13 @@ def test_batch_sizes_range():
     assert len(s) == 64 and min(s) >= 256 and max(s) <= 2048
 
 
-@pytest.mark.parametrize("name,n", [("rect_gaussian", 12), ("toeplitz_folding", 15)])
+@pytest.mark.parametrize("name,n", [("rect_gaussian", 12), ("toeplitz_folding", 15), ("rect_gaussian_short", 16)])
 def test_rect_reduce_keeps_singular_values(name, n):
     """The host reduction of a rectangular C (SM2.2 plus a Schur form of the
-    top block and a QR of R_l U): [T; B] is 2n x n with both blocks upper
-    triangular, and sigma([T - zI; B]) = sigma(C - zI) -- both sides by the
-    oracle, within the reduction's backward error."""
+    top block and a QR of R_l U; a C with n < m < 2n is first extended by zero
+    rows to 2n): [T; B] is 2n x n with both blocks upper triangular, and
+    sigma([T - zI; B]) = sigma(C - zI) -- both sides by the oracle, within the
+    reduction's backward error."""
     import oracle
 
     W = workloads.make(name, n=n, nx=3, ny=3)
@@ -53,6 +54,29 @@ def test_rect_reduce_keeps_singular_values(name, n):
         a, _ = oracle.singular_values(W.C, z)
         b, _ = oracle.singular_values(M, z)
         assert np.max(np.abs(a - b)) <= 8 * W.schur_err + 1e-13 * a.max()
+
+
+@pytest.mark.parametrize("m", [9, 13, 17])
+def test_rect_reduce_short_c(m):
+    """n < m < 2n (n = 9, m = 13 and 17; m = 9 is square and refused): B has
+    only m - n nonzero rows, and the pencil keeps the singular values of the
+    original m x n C - zI at a few shifts."""
+    import oracle
+
+    n = 9
+    C = workloads.rect_gaussian(n, m, 11)
+    if m == n:
+        with pytest.raises(ValueError):
+            workloads.rect_reduce(C)
+        return
+    M, err = workloads.rect_reduce(C)
+    assert M.shape == (2 * n, n)
+    assert np.all(M[n + (m - n):] == 0)
+    for z in (0.3 - 0.2j, -1.1 + 0.4j, 0.0):
+        a, _ = oracle.singular_values(C, z)
+        b, _ = oracle.singular_values(M, z)
+        assert a.shape == b.shape == (n,)
+        assert np.max(np.abs(a - b)) <= 8 * err + 1e-13 * a.max()
 
 
 def test_toeplitz_folding_recipe():
