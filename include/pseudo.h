@@ -209,6 +209,9 @@ int pseudo_workspace_bytes(pseudo_handle h, const pseudo_opts *o, int64_t npts, 
  *   flags_out  : npts int32 PSEUDO_PT_* bits, or NULL.
  *   member_out : npts uint32 words, bit i set iff sigma < eps_levels[i] (strict), or NULL.
  *   workspace  : device memory of >= pseudo_workspace_bytes(...) bytes, 256-byte aligned.
+ * Device arrays must be naturally aligned (z 16 bytes, sigma/res 8, flags/member
+ * 4): a misaligned one gives PSEUDO_ERR_ARG before any work (host arrays, with
+ * o->io_host, need no alignment).
  * Outputs are in the caller's order of z.  No device memory is allocated.
  * Returns OK, WARN_NOT_CONVERGED, or an error. */
 int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double *eps_levels,
@@ -315,7 +318,8 @@ int64_t pseudo_launch_count(void);
  *               cores), PSEUDO_MIXED_CUDACORE (FP32 on the CUDA cores) or
  *               PSEUDO_DOUBLE_SINGLE (double-single arithmetic on the CUDA cores,
  *               about 2^-46 relative per operation).
- *   workspace : device, >= pseudo_solve_workspace_bytes bytes.
+ *   workspace : device, >= pseudo_solve_workspace_bytes bytes, 256-byte aligned.
+ *   X and z must be 16-byte aligned (PSEUDO_ERR_ARG otherwise).
  * pseudo_matvec: Y[:, c] <- B[:, c] - (T - z_c I)^{op} X[:, c] (subtract = 1) or
  *   Y[:, c] <- (T - z_c I)^{op} X[:, c] (subtract = 0, B ignored and may be NULL); the
  *   refinement residual of a shifted solve and the products T V, T^H V of Alg. 2.
@@ -325,8 +329,10 @@ int64_t pseudo_launch_count(void);
  *   double-single (about 2^-50 relative to the row and column maxima);
  *   PSEUDO_MIXED_CUDACORE: double-single arithmetic on the FP32 units (T split into
  *   two FP32 planes, exact products and two-sums; relative error about 2^-46).
- *   X, Y, B device row-major n x ncols complex; Y must not alias X. z may be NULL (z = 0).
- *   workspace : device, >= pseudo_matvec_workspace_bytes bytes (used by PSEUDO_MIXED). */
+ *   X, Y, B device row-major n x ncols complex (16-byte aligned, as is z); Y must not
+ *   alias X. z may be NULL (z = 0).
+ *   workspace : device, >= pseudo_matvec_workspace_bytes bytes, 256-byte aligned (used
+ *   by PSEUDO_MIXED). */
 int pseudo_matvec_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
 int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes);
 int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
@@ -351,7 +357,8 @@ int pseudo_set_wait_limit(pseudo_handle h, uint64_t ns);
  * device-memory budget at start-up, or a latency-critical loop that must not
  * call cudaMalloc/cudaFree because they can synchronise the device).  The paper
  * has no counterpart: it is a library-usage entry point.
- *   X, z, ncols, adjoint, stream : as for pseudo_solve (X device, in place; z device).
+ *   X, z, ncols, adjoint, stream : as for pseudo_solve (X device, in place; z device;
+ *   both 16-byte aligned).
  * Scratch: a fixed 16 MiB array inside the library (2^20 complex doubles), held
  * by every GPU that loads the library until the process exits.  The solve needs
  * ceil(ncols / 8) * n_pad * 8 of its elements (n_pad = n rounded up to 128), so

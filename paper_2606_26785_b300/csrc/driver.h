@@ -13,6 +13,8 @@ constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
 int set_err(int code, const char *fmt, ...);
 int cuda_err(cudaError_t e, const char *where);
 void clear_err();
+// true when p is not a multiple of a (a power of two); NULL is aligned
+bool misaligned(const void *p, uintptr_t a);
 // the tuned table of autotune_table.h: FP32 solver kernel and Lanczos slots for order n
 int tuned_fp32_solver(int n);
 int tuned_slots(int n);

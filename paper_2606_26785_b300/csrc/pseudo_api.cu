@@ -44,6 +44,11 @@ int cuda_err(cudaError_t e, const char *where) {
     return set_err(PSEUDO_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// Device arrays are read with their natural vector widths (complex values as
+// 16-byte pairs, bulk copies of workspace images from 16-byte boundaries), so
+// a misaligned pointer would fault on the device: it is refused on the host.
+bool misaligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; }
+
 // ---------------------------------------------------------- workspace
 void *Carver::take(size_t bytes) {
     size_t off = (used + 255) & ~(size_t)255;
@@ -310,7 +315,8 @@ static int check_dev_err(pseudo_ctx *h, cudaStream_t s) {
 }
 
 int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) {
-    if (!h || !bytes || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    clear_err();
+    if (!h || !bytes || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
     Carver c;
     c.take(trsv_scratch_bytes(1, h->n_pad, ncols));
     c.take((size_t)h->n * ncols * sizeof(float2));
@@ -322,6 +328,8 @@ int pseudo_solve_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) 
 int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint, int precision,
                  void *workspace, size_t workspace_bytes, void *stream) {
     clear_err();
+    if (misaligned(X, 16) || misaligned(z, 16))
+        return set_err(PSEUDO_ERR_ARG, "X and z must be 16-byte aligned (complex doubles)");
     if (!h || !X || !z || ncols < 0 || ncols > (1 << 30)) return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "shifted solves need a square handle (m = n)");
     if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE &&
@@ -331,6 +339,7 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
     size_t need = 0;
     pseudo_solve_workspace_bytes(h, ncols, &need);
     if (!workspace || workspace_bytes < need) return set_err(PSEUDO_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+    if (misaligned(workspace, 256)) return set_err(PSEUDO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c((char *)workspace, workspace_bytes);
     const int lower = adjoint ? 1 : 0;
@@ -362,7 +371,8 @@ int pseudo_solve(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t nc
 }
 
 int pseudo_matvec_workspace_bytes(pseudo_handle h, int64_t ncols, size_t *bytes) {
-    if (!h || !bytes || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
+    clear_err();
+    if (!h || !bytes || ncols < 0 || ncols > (1 << 18)) return set_err(PSEUDO_ERR_ARG, "bad argument");
     *bytes = oz_scratch_bytes(h->n_pad, ncols) + 256;
     return PSEUDO_OK;
 }
@@ -371,6 +381,8 @@ int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pse
                   int64_t ncols, int adjoint, int subtract, int precision, void *workspace, size_t workspace_bytes,
                   void *stream) {
     clear_err();
+    if (misaligned(X, 16) || misaligned(Y, 16) || misaligned(B, 16) || misaligned(z, 16))
+        return set_err(PSEUDO_ERR_ARG, "X, B, Y and z must be 16-byte aligned (complex doubles)");
     if (!h || !X || !Y || ncols < 0 || (subtract && !B)) return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "products with T - zI need a square handle (m = n)");
     if (precision != PSEUDO_FP64 && precision != PSEUDO_MIXED && precision != PSEUDO_MIXED_CUDACORE)
@@ -382,6 +394,7 @@ int pseudo_matvec(pseudo_handle h, const pseudo_c64 *X, const pseudo_c64 *B, pse
         size_t need = 0;
         pseudo_matvec_workspace_bytes(h, ncols, &need);
         if (!workspace || workspace_bytes < need) return set_err(PSEUDO_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+        if (misaligned(workspace, 256)) return set_err(PSEUDO_ERR_WORKSPACE, "workspace must be 256-byte aligned");
     }
     const int lower = adjoint ? 1 : 0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -455,9 +468,14 @@ int pseudo_grid(pseudo_handle h, const pseudo_c64 *z, int64_t npts, const double
                 const pseudo_opts *o, double *sigma_out, double *res_out, int32_t *flags_out, uint32_t *member_out,
                 void *workspace, size_t workspace_bytes, void *stream) {
     clear_err();
-    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
     int rc = check_opts(o);
-    if (!rc) rc = check_rect(h, o);
+    if (rc) return rc;
+    if (!o->io_host && (misaligned(z, 16) || misaligned(sigma_out, 8) || misaligned(res_out, 8) ||
+                        misaligned(flags_out, 4) || misaligned(member_out, 4)))
+        return set_err(PSEUDO_ERR_ARG, "device arrays must be naturally aligned (z 16, sigma/res 8, flags/member 4 "
+                                       "bytes)");
+    if (!h) return set_err(PSEUDO_ERR_ARG, "handle is NULL");
+    rc = check_rect(h, o);
     if (rc) return rc;
     if (npts < 0 || npts >= (int64_t)1 << 31) return set_err(PSEUDO_ERR_ARG, "npts out of range");
     if (npts == 0) return PSEUDO_OK;

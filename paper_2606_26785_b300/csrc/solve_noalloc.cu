@@ -52,6 +52,8 @@ using namespace pseudo;
 extern "C" int pseudo_solve_noalloc(pseudo_handle h, pseudo_c64 *X, const pseudo_c64 *z, int64_t ncols, int adjoint,
                                     void *stream) {
     clear_err();
+    if (misaligned(X, 16) || misaligned(z, 16))
+        return set_err(PSEUDO_ERR_ARG, "X and z must be 16-byte aligned (complex doubles)");
     if (!h || !X || !z || ncols < 0) return set_err(PSEUDO_ERR_ARG, "bad argument");
     if (h->rect) return set_err(PSEUDO_ERR_UNSUPPORTED, "shifted solves need a square handle (m = n)");
     if (ncols == 0) return PSEUDO_OK;

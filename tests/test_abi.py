@@ -96,6 +96,47 @@ def test_argument_errors_are_reported_before_any_device_work():
     assert lib.pseudo_tuned_config(c64(0), None, None) == _abi.ERR_ARG
 
 
+def test_misaligned_device_arrays_are_refused():
+    """Device arrays are read with their natural vector widths, so a
+    misaligned pointer would fault on the device: the host refuses it first
+    (complex arrays 16 bytes, sigma/res 8, flags/member 4), before looking at
+    the handle.  Host arrays (io_host = 1) are only copied and need no such
+    alignment."""
+    from paper_2606_26785_b300 import _abi
+
+    lib = _abi.load()
+    raw = (ctypes.c_char * 256)()
+    a = ctypes.addressof(raw)
+    assert a % 8 == 0
+    good = a if a % 16 == 0 else a + 8
+    odd = good + 8
+    vp, c64 = ctypes.c_void_p, ctypes.c_int64
+    assert lib.pseudo_solve(None, vp(odd), vp(good), c64(1), 0, 0, vp(good), ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    assert b"aligned" in lib.pseudo_last_error()
+    assert lib.pseudo_solve(None, vp(good), vp(odd), c64(1), 0, 0, vp(good), ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    assert b"aligned" in lib.pseudo_last_error()
+    assert lib.pseudo_matvec(None, vp(good), None, vp(odd), None, c64(1), 0, 0, 0, None, ctypes.c_size_t(0),
+                             None) == _abi.ERR_ARG
+    assert b"aligned" in lib.pseudo_last_error()
+    assert lib.pseudo_solve_noalloc(None, vp(odd), vp(good), c64(1), 0, None) == _abi.ERR_ARG
+    assert b"aligned" in lib.pseudo_last_error()
+    o = _abi.Opts()
+    assert lib.pseudo_opts_default(ctypes.byref(o)) == 0
+    for z, sig, flags in ((odd, good, None), (good, good + 4, None), (good, good, good + 2)):
+        assert lib.pseudo_grid(None, vp(z), c64(4), None, 0, ctypes.byref(o), vp(sig), None, vp(flags), None,
+                               vp(good), ctypes.c_size_t(64), None) == _abi.ERR_ARG
+        assert b"aligned" in lib.pseudo_last_error()
+    # aligned arrays get as far as the handle check
+    assert lib.pseudo_grid(None, vp(good), c64(4), None, 0, ctypes.byref(o), vp(good), None, None, None,
+                           vp(good), ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    assert b"handle" in lib.pseudo_last_error()
+    # host arrays are not checked for alignment
+    o.io_host = 1
+    assert lib.pseudo_grid(None, vp(odd), c64(4), None, 0, ctypes.byref(o), vp(odd), None, None, None,
+                           vp(good), ctypes.c_size_t(64), None) == _abi.ERR_ARG
+    assert b"handle" in lib.pseudo_last_error()
+
+
 def test_tuned_table_covers_every_order():
     """The tuned table (pseudo_tuned_config, host-only) gives a valid solver
     kernel and a positive slot count for every order, piecewise constant over
