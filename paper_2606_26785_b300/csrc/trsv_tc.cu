@@ -132,7 +132,7 @@ namespace {
 // at n = 8000, 1.16x (1,184 columns) to 1.31x (9,472 columns) faster; at
 // n = 4000, 1.12x.  At small orders the 128-step diagonal-block solves set
 // the pace instead, and a wide CTA has twice the columns per diagonal warp:
-// at n = 2048 the narrow form is 1.2-1.3x faster, so handles below
+// at n = 256 .. 2048 the narrow form is 1.2-1.6x faster, so handles below
 // TC_WIDE_MIN_NPAD keep it.
 #ifndef TC_WIDE_STAGES
 #define TC_WIDE_STAGES 4   // ring stages of the wide form (3 measured the same; 4 is the most that fits)
