@@ -117,7 +117,8 @@ class Pseudo:
         tensors receive the results (with the same workspace, a repeated call
         then replays the library's cached loop graph)."""
         torch = _torch()
-        o = opts if opts is not None else default_opts(**kw)
+        o = Opts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
+        o.io_host = 0  # the binding hands the library device tensors
         zt = torch.as_tensor(np.asarray(z, dtype=np.complex128)) if not torch.is_tensor(z) else z
         zt = zt.to(device="cuda", dtype=torch.complex128).contiguous()
         npts = zt.numel()
@@ -145,8 +146,8 @@ class Pseudo:
         """Same as grid() but z and the outputs are (pinned) host arrays: the
         library copies them to and from the device inside the call."""
         torch = _torch()
-        o = opts if opts is not None else default_opts(**kw)
-        o.io_host = 1
+        o = Opts.from_buffer_copy(opts) if opts is not None else default_opts(**kw)
+        o.io_host = 1  # a copy: the caller's options are left as they were
         z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
         npts = z.size
         if out is None:
