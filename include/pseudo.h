@@ -137,6 +137,11 @@ typedef struct {
     int64_t lanczos_steps;
     int64_t lobpcg_iters;
     int64_t n_fallback;  /* mixed precision: points handed to the FP64 pass (PSEUDO_PT_IR_FALLBACK) */
+    /* device time in ms, summed over calls: the recycling path's phases in the
+     * paper's breakdown (recySing; LOBPCG-SVD refinement with its start block;
+     * values and residuals of the refined points; updateRecy), each from events
+     * on the call's stream around the phase (0 in inverse-Lanczos mode), and
+     * whole pseudo_grid calls in either mode */
     double ms_recysing, ms_refine, ms_update, ms_polish, ms_total;
     int64_t n_singular;  /* of those, points found singular to working precision (PSEUDO_PT_SINGULAR) */
     int64_t n_rtilde_capped; /* recycle mode: recySing evaluations whose r~ of eq. (tau) exceeded the

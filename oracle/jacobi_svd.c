@@ -7,8 +7,9 @@
  * sigma_min < eps (strict).  Nothing here follows the paper's algorithms; it
  * is the plain definition: form A = C - zI from the ORIGINAL dense matrix C
  * (never from a Schur factor), orthogonalise its columns by complex plane
- * rotations until every pair satisfies |a_i^H a_j| <= tol*||a_i||*||a_j||,
- * and read the singular values off as the column norms.
+ * rotations until every pair satisfies |a_i^H a_j| <= tol*||a_i||*||a_j||
+ * (a column below tol*||A||_F, rounding noise, counts as orthogonal to all:
+ * see rotate_pair), and read the singular values off as the column norms.
  *
  * No LAPACK, no BLAS, no code shared with the CUDA library.  Rotations use a
  * round-robin (tournament) pair ordering so that the n/2 pairs of a round are
@@ -46,12 +47,24 @@ static void col_dots(const ormat *A, int64_t i, int64_t j, double *alpha, double
 }
 
 /* One Hestenes rotation on the column pair (i, j).  Returns the pair's
- * relative off-orthogonality |gamma|/sqrt(alpha*beta) before the rotation. */
-static double rotate_pair(ormat *A, int64_t i, int64_t j, double tol) {
+ * relative off-orthogonality |gamma|/sqrt(alpha*beta) before the rotation, or
+ * 0 for a pair that counts as orthogonal.
+ *
+ * A column whose squared norm is at most small2 = (tol ||A||_F)^2 counts as
+ * orthogonal to every other.  Such a column is rounding noise: floating point
+ * cannot orthogonalise it further (a rotation shrinks it by about one
+ * rounding unit at a time, or leaves its direction noise), so the sweeps
+ * would stall short of the test.  Setting it to zero would move every
+ * singular value by at most its norm (Weyl's bound for a rank-one change),
+ * tol ||A||_F, which is the absolute accuracy the oracle is held to.  Every
+ * column is A Q e_j for a unitary Q, so its norm is at least sigma_min; the
+ * rule therefore acts only where sigma_min(C - zI) <= tol ||C - zI||_F. */
+static double rotate_pair(ormat *A, int64_t i, int64_t j, double tol, double small2) {
     double alpha, beta, gr, gi;
     col_dots(A, i, j, &alpha, &beta, &gr, &gi);
     double g = hypot(gr, gi);
     if (alpha == 0.0 || beta == 0.0 || g == 0.0) return 0.0;
+    if (alpha <= small2 || beta <= small2) return 0.0;
     double rel = g / sqrt(alpha) / sqrt(beta);
     if (rel <= tol) return rel;
     /* Gram of the pair [[alpha, gamma],[conj(gamma), beta]].  Scale column j
@@ -95,6 +108,10 @@ static int jacobi_sweeps(ormat *A, double tol, int max_sweeps, int nthreads, dou
     int64_t np = (n % 2) ? n + 1 : n; /* odd n: one dummy column sits out */
     int64_t *ring = (int64_t *)malloc(sizeof(int64_t) * np);
     for (int64_t k = 0; k < np; k++) ring[k] = k;
+    /* ||A||_F^2, which the rotations keep */
+    double fro2 = 0.0;
+    for (int64_t k = 0; k < A->m * n; k++) fro2 += A->re[k] * A->re[k] + A->im[k] * A->im[k];
+    const double small2 = tol * tol * fro2;
     int sweep = 0;
     double worst = 0.0;
     int64_t rounds_done = 0;
@@ -112,7 +129,7 @@ static int jacobi_sweeps(ormat *A, double tol, int max_sweeps, int nthreads, dou
                 int64_t a = ring[q], b = ring[np - 1 - q];
                 if (a >= n || b >= n) continue;
                 int64_t i = a < b ? a : b, j = a < b ? b : a;
-                double rel = rotate_pair(A, i, j, tol);
+                double rel = rotate_pair(A, i, j, tol, small2);
                 if (rel > wr) wr = rel;
             }
             if (wr > worst) worst = wr;

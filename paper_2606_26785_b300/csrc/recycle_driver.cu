@@ -637,6 +637,45 @@ static int update_slot(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, const
     return (e = cudaGetLastError()) != cudaSuccess ? cuda_err(e, "update") : 0;
 }
 
+// Device time of the phases of Alg. 3 in the paper's breakdown (recySing,
+// LOBPCG-SVD refinement, the refined points' values and residuals, updateRecy),
+// plus the whole call: event pairs recorded on the stream around each phase
+// and read at the next synchronisation of the stream, when they have passed.
+// The events are released on every return path.
+struct PhaseTimes {
+    enum { RECYSING, REFINE, POLISH, UPDATE, TOTAL, NPH };
+    cudaEvent_t ev[NPH][2] = {};
+    bool pending[NPH] = {};
+    bool ok = true;
+    double *acc[NPH];
+    explicit PhaseTimes(pseudo_stats_t &st)
+        : acc{&st.ms_recysing, &st.ms_refine, &st.ms_polish, &st.ms_update, &st.ms_total} {
+        for (auto &pr : ev)
+            for (auto &e : pr)
+                if (cudaEventCreate(&e) != cudaSuccess) { e = nullptr; ok = false; }
+    }
+    ~PhaseTimes() {
+        for (auto &pr : ev)
+            for (auto &e : pr)
+                if (e) cudaEventDestroy(e);
+    }
+    void begin(int ph, cudaStream_t s) { if (ok) cudaEventRecord(ev[ph][0], s); }
+    void end(int ph, cudaStream_t s) {
+        if (!ok) return;
+        cudaEventRecord(ev[ph][1], s);
+        pending[ph] = true;
+    }
+    // call only after the stream has been synchronised
+    void collect() {
+        for (int ph = 0; ph < NPH; ++ph) {
+            if (!pending[ph]) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[ph][0], ev[ph][1]) == cudaSuccess) *acc[ph] += ms;
+            pending[ph] = false;
+        }
+    }
+};
+
 int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c, cudaStream_t s) {
     RecyLayout R;
     recy_layout(h, o, io.npts, c, R, io.on_host);
@@ -644,10 +683,8 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     const int n = h->n;
     const int64_t npts = io.npts;
     cudaError_t e;
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventRecord(ev0, s);
+    PhaseTimes pt(h->stats);
+    pt.begin(PhaseTimes::TOTAL, s);
     const double2 *zall = io.z;
     double *sig_all = io.sigma, *res_all = io.res;
     int32_t *flags_all = io.flags;
@@ -707,6 +744,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         rs.sigma = R.sig_r; rs.res = R.res_r; rs.xi2 = R.xi2_r; rs.w2 = R.w2_r; rs.accept = R.acc_r; rs.rt = R.rt_r;
         rs.CX = R.CX;
         {
+            pt.begin(PhaseTimes::RECYSING, s);
             const int k0 = kp_begin(h, s);
             e = launch_recysing(rs, s);
             // per point: Y and its Gram (2k r + r^2 complex MACs per row, r = block size as a floor for r~),
@@ -715,12 +753,14 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             kp_end(h, k0, PSEUDO_K_RECYSING, np * (8.0 * n * (2 * kf * rf + rf * rf + 8 * kf) + 9 * kf * kf * kf),
                    (double)R.L * 4.0 * n * kf * 16.0, s);
             if (e != cudaSuccess) return cuda_err(e, "recySing");
+            pt.end(PhaseTimes::RECYSING, s);
         }
         acc_h.assign(np, 0);
         rt_h.assign(np, 0);
         cudaMemcpyAsync(acc_h.data(), R.acc_r, np * sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(rt_h.data(), R.rt_r, np * sizeof(int), cudaMemcpyDeviceToHost, s);
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "recySing");
+        pt.collect();
         for (int j = 0; j < np; ++j) h->stats.n_rtilde_capped += rt_h[j] > RTMAX ? 1 : 0;
         note_launch(); scatter_round_kernel<<<(np + 127) / 128, 128, 0, s>>>(nullptr, np, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_ACCEPTED,
                                                               R.eps, io.neps, sig_all, res_all, flags_all, member_all,
@@ -733,6 +773,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         n_ref += nr;
         if (nr == 0) continue;
         // 2. refinement: start from X~ = V C_X (or a seeded random block for an empty subspace)
+        pt.begin(PhaseTimes::REFINE, s);
         cudaMemcpyAsync(R.items, items_h.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s);
         launch_expand_shift(R.zr, R.B, R.r, R.zcol, s);
         {
@@ -756,7 +797,9 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             fprintf(stderr, "[pseudo] round %d: %d points, %d refined, %lld LOBPCG iterations, %d unconverged\n", round,
                     np, nr, (long long)(h->stats.lobpcg_iters - it0), nbad);
         if (nbad < 0) return nbad;
+        pt.end(PhaseTimes::REFINE, s);
         // 3. sigma and residual of the refined points (polished in mixed precision)
+        pt.begin(PhaseTimes::POLISH, s);
         cudaMemcpyAsync(R.items, items_h.data(), nr * sizeof(int), cudaMemcpyHostToDevice, s);
         note_launch(); x1_gather_kernel<<<(nr + 31) / 32, 256, 0, s>>>(R.S, R.Wd, R.r, R.items, nr, n, R.U, R.zr, R.zc, 0);
         launch_normalize(R.U, n, nr, nullptr, s);
@@ -768,7 +811,9 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         note_launch(); scatter_round_kernel<<<(nr + 127) / 128, 128, 0, s>>>(R.items, nr, R.ridx, R.sig_r, R.res_r, PSEUDO_PT_REFINED,
                                                               R.eps, io.neps, sig_all, res_all, flags_all, member_all,
                                                               R.nflag);
+        pt.end(PhaseTimes::POLISH, s);
         // 4. updateRecy per lane in visiting order: slot u = the u-th refined point of each lane
+        pt.begin(PhaseTimes::UPDATE, s);
         std::vector<std::vector<int>> per_lane(R.L);
         for (int j : items_h) per_lane[lane_r[j]].push_back(j);
         size_t nslots = 0;
@@ -780,6 +825,7 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
             const int rc = update_slot(h, o, R, sl, si, s);
             if (rc < 0) return rc;
         }
+        pt.end(PhaseTimes::UPDATE, s);
         for (int l = 0; l < R.L; ++l)
             if (!per_lane[l].empty()) started[l] = 1;
     }
@@ -789,13 +835,9 @@ int recycle_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         if (io.flags) cudaMemcpyAsync(io.flags, flags_all, npts * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (io.member) cudaMemcpyAsync(io.member, member_all, npts * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     }
-    cudaEventRecord(ev1, s);
+    pt.end(PhaseTimes::TOTAL, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "pseudo_grid");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    h->stats.ms_total += ms;
+    pt.collect();
     h->stats.n_points += npts;
     h->stats.n_accepted += n_acc;
     h->stats.n_refined += n_ref;

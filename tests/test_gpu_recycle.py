@@ -3,7 +3,9 @@ Jacobi-SVD oracle, plus algebraic facts that hold at any size:
 
 * a full basis (k = n on a tiny matrix) makes the recycled Ritz value exact;
 * every accepted Ritz value is an upper bound of sigma_min (Courant--Fischer);
-* the counter identity mv_M = 3 r * (#updates) of Table 2.
+* the counter identity mv_M = 3 r * (#updates) of Table 2;
+* the per-phase times (recySing, refinement, values, updateRecy) are filled
+  and add up to no more than the call.
 """
 import numpy as np
 import pytest
@@ -47,6 +49,11 @@ def test_grcar_recycle_full_grid(grcar, precision, rtol):
     assert rep["member_mismatch"] == 0, rep
     assert st["n_accepted"] + st["n_refined"] == W.z.size
     assert st["mv_M"] == 3 * 4 * st["n_updates"]
+    # per-phase device time in the paper's breakdown: every phase ran, and the
+    # phases (disjoint stretches of the stream) fit inside the whole call
+    phases = [st[k] for k in ("ms_recysing", "ms_refine", "ms_polish", "ms_update")]
+    assert all(t > 0.0 for t in phases), st
+    assert sum(phases) <= st["ms_total"] * 1.001 + 1e-3, st
 
 
 @pytest.mark.parametrize("traversal", [1, 2])

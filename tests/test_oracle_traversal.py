@@ -91,7 +91,7 @@ def test_library_order_matches_oracle_on_random_grids():
 
     import paper_2606_26785_b300 as p
 
-    @settings(max_examples=300, deadline=None)
+    @settings(max_examples=300, deadline=None, derandomize=True)
     @given(st.integers(1, 90), st.integers(1, 90), st.integers(1, 100))
     def check(nx, ny, b):
         assert p.traversal_order(nx, ny, b).tolist() == batch_zigzag(nx, ny, b)
