@@ -517,7 +517,8 @@ def main():
     kst = h.kernel_stats()
     prof_ms = h.stats()["ms_total"]
     solver = opts.fp32_solver if opts.fp32_solver != p._abi.SOLVER_AUTO else p.tuned_config(W.n)["fp32_solver"]
-    rf = roofline(kst, peaks, W.n, tensor_solve=solver == 0)
+    rf = roofline(kst, peaks, W.n, tensor_solve=solver in (p._abi.SOLVER_TENSOR_CORES, p._abi.SOLVER_TC16,
+                                                           p._abi.SOLVER_TC32))
     if rf is not None:
         rf["share_of_step"] = max(kst.values(), key=lambda v: v["ms"])["ms"] / max(prof_ms, 1e-9)
 

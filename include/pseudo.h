@@ -64,6 +64,10 @@ enum { PSEUDO_MIXED_CUDACORE = 2 };
 enum { PSEUDO_DOUBLE_SINGLE = 3 };
 /* pseudo_opts.fp32_solver: chosen per matrix order from the tuned table */
 enum { PSEUDO_SOLVER_AUTO = 2 };
+/* pseudo_opts.fp32_solver: the tensor-core solve in a fixed form, 16 right-hand
+ * sides per CTA (2-stage copy ring, two CTAs per SM) or 32 (4-stage ring, one
+ * CTA per SM); plain 0 takes the 32-column form from padded order 4096 up */
+enum { PSEUDO_SOLVER_TC16 = 3, PSEUDO_SOLVER_TC32 = 4 };
 
 /* grid traversal of the recycling path (pseudo_opts.traversal):
  * BATCH_ZIGZAG = the batch-zigzag order of Sec. 2.3 with column batches of
@@ -113,10 +117,11 @@ typedef struct {
     uint64_t seed;      /* seed of the random start vectors */
     int profile;        /* 1: time every hot-kernel launch with CUDA events (pseudo_kernel_stats) */
     int fp32_solver;    /* mixed precision: the FP32 triangular solves run on 0 = the tensor
-                           cores (tcgen05, operands split hi + lo into TF32, 3 products),
-                           1 = the CUDA cores (FP32 FMA), PSEUDO_SOLVER_AUTO (default) = the
-                           choice of the library's tuned table for the matrix order
-                           (pseudo_tuned_config) */
+                           cores (tcgen05, operands split hi + lo into TF32, 3 products;
+                           16 or 32 right-hand sides per CTA by order), PSEUDO_SOLVER_TC16 /
+                           PSEUDO_SOLVER_TC32 = the tensor cores in that form, 1 = the CUDA
+                           cores (FP32 FMA), PSEUDO_SOLVER_AUTO (default) = the choice of the
+                           library's tuned table for the matrix order (pseudo_tuned_config) */
     int traversal;      /* RECYCLE on a Cartesian grid: the visiting order, PSEUDO_TRAVERSE_* */
     int device_loop;    /* INVLANC: 1 (default) = the Lanczos driver's loop runs on the device,
                            captured once per call as a CUDA graph whose conditional nodes
@@ -286,8 +291,9 @@ int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, 
 
 /* The library's tuned choices for a matrix of order n (the benchmark spec batching
  * pattern's autotuner; the paper has no counterpart): the FP32 solver kernel
- * that pseudo_opts.fp32_solver = PSEUDO_SOLVER_AUTO selects (0 tensor cores,
- * 1 CUDA cores) and the number of Lanczos slots (shifts per solve launch)
+ * that pseudo_opts.fp32_solver = PSEUDO_SOLVER_AUTO selects (0 tensor cores in
+ * the form the order picks, PSEUDO_SOLVER_TC16 / TC32 tensor cores in that
+ * form, 1 CUDA cores) and the number of Lanczos slots (shifts per solve launch)
  * that shift_batch = 0 selects in inverse-Lanczos mode.  The table comes from
  * an offline sweep on this part, per bucket of n.  Either pointer may be NULL.
  * Host-only.  Errors: ARG (n < 1). */

@@ -12,7 +12,7 @@ ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT = 
 INVLANC, RECYCLE = 0, 1
 FP64, MIXED, MIXED_CUDACORE, DOUBLE_SINGLE = 0, 1, 2, 3
 TRAVERSE_BATCH_ZIGZAG, TRAVERSE_HILBERT, TRAVERSE_MORTON = 0, 1, 2
-SOLVER_TENSOR_CORES, SOLVER_CUDA_CORES, SOLVER_AUTO = 0, 1, 2
+SOLVER_TENSOR_CORES, SOLVER_CUDA_CORES, SOLVER_AUTO, SOLVER_TC16, SOLVER_TC32 = 0, 1, 2, 3, 4
 PT_ACCEPTED, PT_REFINED, PT_NOT_CONVERGED, PT_IR_FALLBACK, PT_SINGULAR = 1, 2, 4, 8, 16
 
 EXPORTED = (

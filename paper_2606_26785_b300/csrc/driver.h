@@ -72,7 +72,8 @@ struct pseudo_ctx {
     // (64-row tile, 16-column chunk) image, and the per-row scale exponents
     void *ozA_U = nullptr, *ozA_L = nullptr;
     int *ozE_U = nullptr, *ozE_L = nullptr;
-    int fp32_solver = 0;                     // 0 tensor cores, 1 CUDA cores
+    int fp32_solver = 0;                     // 0 tensor cores (form by order), 1 CUDA cores,
+                                             // PSEUDO_SOLVER_TC16 / TC32 tensor cores in that form
     // rectangular input (m = 2n, SM2.2): M = [T; B] dense column-major (2n x n,
     // leading dimension 2n) and the FP64 panels of B and B^H
     bool rect = false;

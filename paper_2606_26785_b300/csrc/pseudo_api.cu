@@ -418,7 +418,7 @@ static int check_opts(const pseudo_opts *o) {
         return set_err(PSEUDO_ERR_ARG, "maxiter_lanczos must be in [1, %d]", LANCZOS_MMAX);
     if (o->max_ir < 1 || o->max_ir > 32) return set_err(PSEUDO_ERR_ARG, "max_ir must be in [1, 32]");
     if (o->shift_batch < 0) return set_err(PSEUDO_ERR_ARG, "shift_batch < 0");
-    if (o->fp32_solver < 0 || o->fp32_solver > PSEUDO_SOLVER_AUTO) return set_err(PSEUDO_ERR_ARG, "bad fp32_solver");
+    if (o->fp32_solver < 0 || o->fp32_solver > PSEUDO_SOLVER_TC32) return set_err(PSEUDO_ERR_ARG, "bad fp32_solver");
     if (o->device_loop != 0 && o->device_loop != 1) return set_err(PSEUDO_ERR_ARG, "device_loop must be 0 or 1");
     if (!(o->rtol >= 0.0)) return set_err(PSEUDO_ERR_ARG, "rtol < 0");
     if (o->mode == PSEUDO_RECYCLE) {

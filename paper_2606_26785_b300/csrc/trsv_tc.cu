@@ -509,9 +509,14 @@ static cudaError_t launch_tc(const pseudo_ctx *h, int lower, const int *cols, co
     return cudaGetLastError();
 }
 
+// the FP32 solver codes that run the tensor-core solve (pseudo_opts.fp32_solver)
+static bool tc_solver(int code) { return code == 0 || code == PSEUDO_SOLVER_TC16 || code == PSEUDO_SOLVER_TC32; }
+
 cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                            const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
-    if (h->n_pad >= TC_WIDE_MIN_NPAD)
+    const bool wide = h->fp32_solver == PSEUDO_SOLVER_TC32 ||
+                      (h->fp32_solver != PSEUDO_SOLVER_TC16 && h->n_pad >= TC_WIDE_MIN_NPAD);
+    if (wide)
         return launch_tc<NC_WIDE, NS_WIDE>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return launch_tc<NC_NARROW, NS_NARROW>(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
 }
@@ -519,14 +524,14 @@ cudaError_t launch_trsv_tc(const pseudo_ctx *h, int lower, const int *cols, cons
 cudaError_t solve32(const pseudo_ctx *h, int lower, const int *cols, const double2 *zc, int ncols,
                     const int *ncols_dev, float2 *X, int64_t ldx, float2 *xs, cudaStream_t s) {
     // the scratch (trsv32_scratch_bytes) covers every kernel's column groups
-    if (h->fp32_solver == 0 && h->tcA_U)
+    if (tc_solver(h->fp32_solver) && h->tcA_U)
         return launch_trsv_tc(h, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
     return launch_trsv32(lower ? h->L32 : h->U32, h->n, h->n_pad, lower, cols, zc, ncols, ncols_dev, X, ldx, xs, s);
 }
 
 // 3xTF32 products carry about 2^-22 relative error against FP32's 2^-24
 double solve32_unit_roundoff(const pseudo_ctx *h) {
-    return (h->fp32_solver == 0 && h->tcA_U) ? 2.4e-7 : 5.96e-8;
+    return (tc_solver(h->fp32_solver) && h->tcA_U) ? 2.4e-7 : 5.96e-8;
 }
 
 }  // namespace pseudo

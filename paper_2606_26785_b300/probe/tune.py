@@ -6,7 +6,8 @@ range of the multi-matrix workload; dense complex Gaussian N(0, 1/n), seed
 inverse-Lanczos path on a 64 x 64 grid over [-1.5, 1.5]^2 for every
 combination of
 
-  * the FP32 solver kernel: 0 tensor cores (tcgen05, 3xTF32), 1 CUDA cores;
+  * the FP32 solver kernel: the tensor cores (tcgen05, 3xTF32) with 16 (3) or
+    32 (4) right-hand sides per CTA, or the CUDA cores (1);
   * the number of Lanczos slots (shifts per solve launch);
 
 and keep the fastest per bucket.  With --write the table is rewritten (the
@@ -27,6 +28,7 @@ HERE = Path(__file__).resolve().parent
 TABLE = HERE.parent / "csrc" / "autotune_table.h"
 ORDERS = (256, 362, 512, 724, 1024, 1448, 2048)
 SLOTS = (1024, 2048, 4096, 8192)
+SOLVERS = (3, 4, 1)  # tensor cores 16 and 32 columns per CTA, CUDA cores
 
 
 def sweep(orders, repeats=2):
@@ -41,7 +43,7 @@ def sweep(orders, repeats=2):
         T, _, _ = workloads.schur(workloads.gaussian(n, 100 + n))
         h = p.Pseudo(T)
         best = None
-        for solver in (0, 1):
+        for solver in SOLVERS:
             for slots in SLOTS:
                 o = p.default_opts(mode=p.INVLANC, precision=p.MIXED, rtol=1e-8, fp32_solver=solver,
                                    shift_batch=slots)
@@ -84,14 +86,16 @@ def table_text(rows, orders, gpu):
     return "\n".join([
         "// Tuned choices of the mixed-precision inverse-Lanczos path per matrix order,",
         "// written by paper_2606_26785_b300/probe/tune.py (an offline sweep over the FP32",
-        "// solver kernel and the number of Lanczos slots on one GPU).  Entry i applies",
-        "// to n <= n_max[i] (the last entry to every larger n).",
+        "// solver kernel, with the tensor-core solve's column-group form, and the number",
+        "// of Lanczos slots on one GPU).  Entry i applies to n <= n_max[i] (the last",
+        "// entry to every larger n).",
         f"// sweep: {gpu}, {stamp}; 64 x 64 grid, mixed precision, rtol 1e-8",
         "#pragma once",
         "namespace pseudo {",
         "struct TunePoint {",
         "    int n_max;        // largest matrix order of the bucket",
-        "    int fp32_solver;  // 0 tensor cores (tcgen05), 1 CUDA cores",
+        "    int fp32_solver;  // 0 tensor cores (form by order), 1 CUDA cores, 3 / 4 tensor cores,",
+        "                      // 16 / 32 right-hand sides per CTA",
         "    int slots;        // Lanczos slots (shifts per solve launch)",
         "};",
         "static const TunePoint kTuneTable[] = {",

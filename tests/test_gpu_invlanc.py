@@ -38,6 +38,24 @@ def test_grcar_full_grid(grcar, precision, rtol):
     h.close()
 
 
+@pytest.mark.parametrize("solver", [1, 3, 4])
+def test_grcar_mixed_every_fp32_solver(grcar, solver):
+    """Mixed precision with each FP32 solver forced (CUDA cores; tensor cores
+    with 16 or 32 right-hand sides per CTA, the column-group forms the tuned
+    table chooses between): every grid point against the oracle at 1e-8,
+    identical membership."""
+    import paper_2606_26785_b300 as p
+
+    W, ref, off = grcar
+    h = p.Pseudo(W.T)
+    out = h.grid(W.z, EPS, mode=p.INVLANC, precision=p.MIXED, rtol=1e-8, fp32_solver=solver)
+    rep = check_sigma(out["sigma"].cpu().numpy(), ref, n=W.n, fro=np.linalg.norm(W.C), schur_err=W.schur_err,
+                      oracle_off=off, rtol=1e-8, eps_levels=EPS, member=out["member"].cpu().numpy())
+    print(solver, rep)
+    assert rep["n_bad"] == 0 and rep["member_mismatch"] == 0, rep
+    h.close()
+
+
 def test_host_io_matches_device_io(grcar):
     import paper_2606_26785_b300 as p
 
