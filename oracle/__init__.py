@@ -20,6 +20,11 @@ Contents
     the recycled Rayleigh--Ritz-SVD (Alg. 1) and the recycle-subspace update
     (Alg. 2) written out step by step in NumPy, used to check intermediate
     quantities of the GPU path on small cases.
+``precond_ref``
+    the preconditioned path of Sec. 3 (the two-level preconditioner of eq.
+    (twolevel), Alg. 4 recyProj, Alg. 5 psPrecRecy with a preconditioned
+    LOBPCG-SVD) for a dense C without a Schur factor, written out in NumPy;
+    the CUDA library does not implement this path.
 ``traversal.batch_zigzag(nx, ny, b)``
     the batch-zigzag visiting order of a Cartesian grid (Sec. 2.3, eq.
     (batch)), pinned in ``tests/test_oracle_traversal.py``.
