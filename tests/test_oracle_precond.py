@@ -144,3 +144,31 @@ def test_ps_prec_recy_against_the_jacobi_oracle(name, n, eta):
     assert st["accepted"] + st["refined"] == W.z.size
     assert np.all(sig >= ref - 64 * n * 2.2e-16 * norms)
     assert np.all(sig - ref <= eta * norms + 64 * n * 2.2e-16 * norms)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_projection_pruning_agrees_with_the_block_triangular_form(seed):
+    """Eq. (omegaCond) computed two ways: ProjState.update takes the projection
+    errors from their definition (fresh bases of the kept blocks), Alg. 2 as
+    restated in recycle_ref tracks them through its block-lower-triangular
+    factor.  With S_bar = I (F = I) and the same blocks, both drop the same
+    number of blocks and keep the same span."""
+    from oracle import recycle_ref as rr
+
+    rng = np.random.default_rng(40 + seed)
+    n, r, nb = 16, 2, 5
+    C = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    ps = pr.ProjState(C, np.eye(n, dtype=np.complex128))
+    st = rr.RecycleState(T=C, r=r)
+    base = np.linalg.qr(rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r)))[0]
+    for j in range(nb):
+        # slowly drifting blocks, so that some pruning counts are 0 and some larger
+        X = base + (0.05 + 0.3 * (seed % 3)) * j * (rng.standard_normal((n, r)) + 1j * rng.standard_normal((n, r)))
+        X, _ = np.linalg.qr(X)
+        l1 = ps.update(X, 1.6, 1, 4)
+        l2, skipped = rr.update_recy(st, X, 1.6, 4, rb=1)
+        assert (l1 == -1) == skipped
+        if not skipped:
+            assert l1 == l2
+        Vp = ps.V
+        assert np.linalg.norm(st.V - Vp @ (Vp.conj().T @ st.V)) <= 1e-10
