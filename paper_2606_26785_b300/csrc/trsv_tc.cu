@@ -211,6 +211,7 @@ trsv_tc_kernel(const float *__restrict__ Apack, const float2 *__restrict__ Dblk,
                const int *__restrict__ ncols_dev, float2 *X, int64_t ldx, float2 *xs_all, int *err,
                uint64_t wait_ns) {
     using L = TcSmem<NC, NS>;
+    static_assert(L::bytes + 1024 <= 227 * 1024, "ring and turnaround buffers exceed the shared memory of a CTA");
     constexpr int NR = L::NR;
     constexpr int LBO_A = (MB / 8) * 128, LBO_B = (NR / 8) * 128;
     static_assert(NR % 32 == 0, "the diagonal warps read the accumulator in 32-column pieces");
