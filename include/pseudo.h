@@ -289,8 +289,8 @@ int pseudo_recycle_state_layout(pseudo_handle h, const pseudo_opts *o, int64_t n
 int pseudo_traversal_order(int64_t npts, int grid_nx, int grid_ny, int batch_b, int traversal,
                            int32_t *order);
 
-/* The library's tuned choices for a matrix of order n (the benchmark spec batching
- * pattern's autotuner; the paper has no counterpart): the FP32 solver kernel
+/* The library's tuned choices for a matrix of order n (the autotuner of the
+ * multi-matrix batching; the paper has no counterpart): the FP32 solver kernel
  * that pseudo_opts.fp32_solver = PSEUDO_SOLVER_AUTO selects (0 tensor cores in
  * the form the order picks, PSEUDO_SOLVER_TC16 / TC32 tensor cores in that
  * form, 1 CUDA cores) and the number of Lanczos slots (shifts per solve launch)
