@@ -70,3 +70,33 @@ def test_clock_summary(tmp_path):
     c = bench.Clocks(str(f)).summary()
     assert c["sm_mhz"] == 2032.0 and c["sm_max_mhz"] == 2032.0 and c["samples"] == 4
     assert c["reasons"] == ["sw_power_cap"]
+
+
+def test_compare_with_fp64_rule():
+    """The bench's mixed-against-FP64 check: relative target with the n eps
+    ||T||_F floor above 1e-8 ||T||_F, the relative target alone above 1e-6
+    ||T||_F, nothing below 1e-8 ||T||_F, and membership compared outside the
+    levels' bands."""
+    import numpy as np
+
+    fro, n = 100.0, 1000
+    s64 = np.array([1.0, 1e-3, 5e-5, 2e-6, 1e-12])
+    ok = s64 * (1 + 5e-9)
+    rep = bench.compare_with_fp64(ok, s64, fro, n)
+    assert rep["n_bad"] == 0 and rep["n_included"] == 4 and rep["n_rel_only"] == 2
+    bad = s64.copy()
+    bad[1] *= 1 + 2e-8            # above 1e-6 ||T||_F: the relative target alone fails it
+    bad[4] = 1.0                  # below 1e-8 ||T||_F: not compared
+    rep = bench.compare_with_fp64(bad, s64, fro, n)
+    assert rep["n_bad"] == 1
+    # a value between 1e-8 and 1e-6 ||T||_F may use the absolute floor 4 n eps ||T||_F
+    floor = 4 * n * 2.220446049250313e-16 * fro
+    near = s64.copy()
+    near[3] = s64[3] + 0.9 * floor
+    assert bench.compare_with_fp64(near, s64, fro, n)["n_bad"] == 0
+    eps_levels = (1e-2, 1e-4)
+    mem64 = np.array([0, 1, 3, 3, 3], dtype=np.uint32)
+    mem = mem64.copy()
+    mem[0] = 1                    # sigma = 1 against level 1e-2: far outside the band
+    rep = bench.compare_with_fp64(s64, s64, fro, n, member=mem, member64=mem64, eps_levels=eps_levels)
+    assert rep["member_mismatch"] == 1
