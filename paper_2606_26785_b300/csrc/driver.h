@@ -1,6 +1,7 @@
 // Handle layout, workspace carving and grid-driver entry points (host side).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -8,6 +9,15 @@
 #include "internal.h"
 
 namespace pseudo {
+// A named range on a profiler's NVTX timeline for the scope it lives in (the
+// phases of the grid drivers, named as in the paper's time breakdown); it does
+// nothing when no profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 struct GraphCache;  // instantiated device-loop graphs of a handle (invlanc.cu)
 constexpr int RECY_KMAX = 64;  // largest recycled rank k = p_max * r supported
 int set_err(int code, const char *fmt, ...);

@@ -766,7 +766,11 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
         member_all = io.member ? L.member_dev : nullptr;
     }
     if (io.neps > 0) cudaMemcpyAsync(L.eps, io.eps_host, io.neps * sizeof(double), cudaMemcpyHostToDevice, s);
-    int rc = run_points(h, o, L, zall, npts, io.neps, sig_all, res_all, flags_all, member_all, s);
+    int rc;
+    {
+        NvtxRange nr("inverse Lanczos");
+        rc = run_points(h, o, L, zall, npts, io.neps, sig_all, res_all, flags_all, member_all, s);
+    }
     if (rc < 0) return rc;
     int nbad = 0, nfb = 0;
     cudaMemcpyAsync(&nbad, L.nbad, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -779,10 +783,12 @@ int invlanc_run(pseudo_ctx *h, const pseudo_opts *o, const GridIO &io, Carver &c
     if (nfb > 0) {
         double min_level = HUGE_VAL;
         for (int i = 0; i < io.neps; ++i) min_level = std::min(min_level, io.eps_host[i]);
+        NvtxRange nr("singular-to-working-precision test");
         rc = fallback_triage(h, o, L, Lfb, zall, io.neps, min_level, sig_all, res_all, flags_all, member_all, nfb,
                              compacted, s);
         if (rc < 0) return rc;
     }
+    NvtxRange nr_fb("inverse Lanczos, FP64 pass");
     for (int off = 0; off < nfb; off += L.CH) {
         const int cnt = std::min(L.CH, nfb - off);
         if (io.neps > 0) cudaMemcpyAsync(Lfb.eps, L.eps, io.neps * sizeof(double), cudaMemcpyDeviceToDevice, s);

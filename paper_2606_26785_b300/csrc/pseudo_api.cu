@@ -103,6 +103,7 @@ int pseudo_create(const pseudo_c64 *T, int64_t ldT, int64_t m, int64_t n, int t_
     if (m == 2 * n && n > rect_max_order())
         return set_err(PSEUDO_ERR_UNSUPPORTED, "a rectangular pencil needs n <= %d", rect_max_order());
     cudaStream_t s = (cudaStream_t)stream;
+    NvtxRange nr("pseudo_create: packed copies of T, norms");
     pseudo_ctx *h = new pseudo_ctx();
     h->n = (int)n;
     h->rect = m == 2 * n;

@@ -644,9 +644,12 @@ static int update_slot(pseudo_ctx *h, const pseudo_opts *o, RecyLayout &R, const
 // The events are released on every return path.
 struct PhaseTimes {
     enum { RECYSING, REFINE, POLISH, UPDATE, TOTAL, NPH };
+    static constexpr const char *name[NPH] = {"recySing", "lobpcgSvd", "refined values", "updateRecy",
+                                              "psTriRecy"};
     cudaEvent_t ev[NPH][2] = {};
     bool pending[NPH] = {};
     bool ok = true;
+    int open = 0;  // NVTX ranges pushed and not yet popped
     double *acc[NPH];
     explicit PhaseTimes(pseudo_stats_t &st)
         : acc{&st.ms_recysing, &st.ms_refine, &st.ms_polish, &st.ms_update, &st.ms_total} {
@@ -658,9 +661,17 @@ struct PhaseTimes {
         for (auto &pr : ev)
             for (auto &e : pr)
                 if (e) cudaEventDestroy(e);
+        while (open > 0) { nvtxRangePop(); --open; }  // a return inside a phase
     }
-    void begin(int ph, cudaStream_t s) { if (ok) cudaEventRecord(ev[ph][0], s); }
+    // each phase is also a range on a profiler's NVTX timeline
+    void begin(int ph, cudaStream_t s) {
+        nvtxRangePushA(name[ph]);
+        ++open;
+        if (ok) cudaEventRecord(ev[ph][0], s);
+    }
     void end(int ph, cudaStream_t s) {
+        nvtxRangePop();
+        --open;
         if (!ok) return;
         cudaEventRecord(ev[ph][1], s);
         pending[ph] = true;
